@@ -1,0 +1,188 @@
+/*
+ * klmc.h -- C ABI of the GB300 Kawasaki lattice Monte Carlo library (libklmc.so).
+ *
+ * The library simulates the paper's model: M. Lis, L. Pintal, "GPU-Based Massive
+ * Parallel Kawasaki Kinetics in Monte Carlo Modelling of Lipid Microdomains"
+ * (arXiv:1309.4349).  A two-component (A/B) lipid lattice, one lipid per site,
+ * evolves by Metropolis-accepted nearest-neighbour exchanges (Kawasaki kinetics)
+ * with energy omega per unlike contact, and is analysed by cluster-size
+ * statistics of one lipid species.
+ *
+ * Conventions for every call:
+ *  - Every call returns a klmc_status; nothing is thrown across the ABI.  On
+ *    error, out-parameters are left untouched unless a call states otherwise,
+ *    and klmc_last_error() returns a message for the calling thread.
+ *  - Device memory is owned by the library and freed by klmc_destroy /
+ *    klmc_batch_destroy.  Host buffers, device buffers passed in by the caller,
+ *    the caller's allocator and the caller's stream stay owned by the caller.
+ *  - Work is enqueued on the handle's CUDA stream.  Calls that return data in
+ *    host memory synchronise that stream first; the others return after enqueue.
+ *  - A handle is used by one host thread at a time.
+ *  - Lattice layout seen by the caller: one byte per site, 1 = A, 0 = B,
+ *    site (x, y) at index y*Lx + x.  Geometry: triangular (six neighbours
+ *    (+-1,0), (0,+-1), (1,-1), (-1,1)) or square (four), periodic in x and y.
+ */
+#ifndef KLMC_H
+#define KLMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum klmc_status {
+    KLMC_OK = 0,
+    KLMC_EINVAL = 1,   /* invalid argument                                   */
+    KLMC_ENOMEM = 2,   /* device or host allocation failed                   */
+    KLMC_ECUDA = 3,    /* a CUDA runtime call failed                         */
+    KLMC_ETIMEOUT = 4, /* a bounded device-side wait gave up                 */
+    KLMC_EBUSY = 5,    /* not admitted now, or a result is still pending     */
+    KLMC_ETRUNC = 6,   /* output capacity too small; needed length reported  */
+    KLMC_ESTATE = 7,   /* call not valid for this handle in its state        */
+    KLMC_ENODEV = 8    /* no usable CUDA device of compute capability 10.3   */
+} klmc_status;
+
+enum { KLMC_TRI6 = 0, KLMC_SQ4 = 1 };                 /* geometry  */
+enum { KLMC_PERIODIC = 0 };                           /* boundary  */
+enum { KLMC_PACK_AUTO = 0, KLMC_PACK_BIT = 1, KLMC_PACK_BYTE = 2 }; /* device store */
+
+/* Caller-supplied device allocator (e.g. a framework's caching allocator).
+ * alloc returns NULL on failure; free receives the size passed to alloc. */
+typedef void *(*klmc_alloc_fn)(size_t bytes, void *stream, void *user);
+typedef void (*klmc_free_fn)(void *ptr, size_t bytes, void *stream, void *user);
+
+/* Model and storage parameters (section "Monte Carlo model with Kawasaki based
+ * kinetics": lattice, binary composition, the single parameter omega_AB). */
+typedef struct klmc_params {
+    int32_t Lx, Ly;        /* lattice sides, each >= 4; Lx*Ly <= 2^31 - 1        */
+    int32_t geometry;      /* KLMC_TRI6 (the paper's lattice) or KLMC_SQ4        */
+    int32_t boundary;      /* KLMC_PERIODIC                                      */
+    int32_t packing;       /* device store: KLMC_PACK_BIT (1 bit/site), _BYTE, or
+                              _AUTO (= BIT)                                       */
+    int32_t reserved0;
+    int64_t n_A;           /* number of A lipids; -1 = floor(fraction_A*N + 0.5)  */
+    double fraction_A;     /* used when n_A < 0; in [0, 1]                        */
+    double omega_over_kT;  /* omega_AB / kT, finite; E/kT = omega/kT * n_unlike   */
+    uint64_t seed;         /* keys every random number of the run (Philox key)   */
+    klmc_alloc_fn alloc;   /* NULL = stream-ordered cudaMallocAsync               */
+    klmc_free_fn free;     /* required when alloc is set                          */
+    void *user;            /* passed to alloc/free                                */
+    void *stream;          /* cudaStream_t for all work; NULL = default stream    */
+} klmc_params;
+
+/* Exact integer counters since creation (or the last klmc_set_lattice).
+ * attempts: pair proposals; unlike: proposals of an A-B pair; draws: random
+ * numbers drawn (only for moves that raise the energy when omega > 0);
+ * accepts: accepted exchanges.  sweeps is the absolute sweep index. */
+typedef struct klmc_counters {
+    int64_t sweeps, attempts, unlike, draws, accepts;
+} klmc_counters;
+
+typedef struct klmc_ctx klmc_ctx;
+typedef struct klmc_batch klmc_batch;
+
+/* Fills p with defaults: 64x64 TRI6 periodic, bit store, n_A = -1,
+ * fraction 0.5, omega/kT 0, seed 1, library allocator, default stream. */
+klmc_status klmc_params_default(klmc_params *p);
+
+/* Creates an L x L triangular lattice with floor(composition_A*L*L + 0.5) A lipids
+ * placed uniformly at random from seed (Fig. 2: randomly distributed lipids).
+ * Equivalent to klmc_create_ex with defaults otherwise. */
+klmc_status klmc_create(klmc_ctx **out, int32_t L, double composition_A, double omega_over_kT,
+                        uint64_t seed);
+
+/* Creates a lattice from full parameters.  The initial placement makes the
+ * n_A sites with the smallest 64-bit Philox keys (ties by site index) A, which
+ * is a uniformly random subset.  EINVAL on Lx or Ly < 4, N > 2^31 - 1, n_A
+ * outside [0, N], fraction outside [0, 1], non-finite omega, or an unknown
+ * geometry/boundary/packing; ENODEV without a compute-capability-10.3 GPU. */
+klmc_status klmc_create_ex(klmc_ctx **out, const klmc_params *p);
+
+/* Enqueues n_mcs Monte Carlo steps (n_mcs >= 0).  One step is eight conflict-free
+ * phases of exchange attempts, N attempts when 4 | Lx and 4 | Ly (section
+ * "Massive Parallel Kawasaki Kinetics": one MPKK step = as many attempts as
+ * sites).  Deterministic: the result depends only on seed, the lattice and the
+ * absolute sweep index.  EINVAL when the lattice is too large for the
+ * shared-memory resident path (padded bit rows must fit one CTA). */
+klmc_status klmc_sweep(klmc_ctx *c, int64_t n_mcs);
+
+/* As klmc_sweep, and records n_unlike after every trace_every-th step into the
+ * caller's device buffer dev_trace (int64, n_mcs / trace_every entries). */
+klmc_status klmc_sweep_traced(klmc_ctx *c, int64_t n_mcs, int64_t trace_every,
+                              int64_t *dev_trace);
+
+/* Number of unlike contacts (kept exactly, updated by every accepted exchange)
+ * and E/kT = omega/kT * n_unlike (energy model of the omega_AB equation).
+ * Synchronises.  Either pointer may be NULL. */
+klmc_status klmc_energy(klmc_ctx *c, int64_t *n_unlike, double *energy_over_kT);
+
+/* Recounts n_unlike from the lattice on the device (every bond once) without
+ * changing the running value.  Synchronises. */
+klmc_status klmc_energy_recount(klmc_ctx *c, int64_t *n_unlike);
+
+/* Sparse cluster-size histogram of the given species (1 = A, 0 = B): connected
+ * components under the lattice adjacency with periodic wrap (section "Cluster
+ * Analysis methods").  Writes (sizes[k], counts[k]) in ascending size to host
+ * buffers and *n_distinct.  ETRUNC (with *n_distinct = needed length, other
+ * outputs untouched) when capacity is too small.  Synchronises. */
+klmc_status klmc_cluster_histogram(klmc_ctx *c, int32_t species, int64_t *sizes, int64_t *counts,
+                                   int64_t capacity, int64_t *n_distinct);
+
+/* Device-side variant: enqueues the same histogram into caller device buffers
+ * (int64) and returns without synchronising.  *dev_n_distinct receives the
+ * number of distinct sizes; only the first min(capacity, n) pairs are written. */
+klmc_status klmc_cluster_histogram_device(klmc_ctx *c, int32_t species, int64_t *dev_sizes,
+                                          int64_t *dev_counts, int64_t capacity,
+                                          int64_t *dev_n_distinct);
+
+/* Counters (see klmc_counters).  Synchronises. */
+klmc_status klmc_get_counters(klmc_ctx *c, klmc_counters *out);
+
+/* Copies the lattice to host memory, one byte per site (n must equal Lx*Ly).
+ * Synchronises. */
+klmc_status klmc_get_lattice(klmc_ctx *c, uint8_t *host_out, int64_t n);
+
+/* Replaces the lattice from host memory (n = Lx*Ly bytes, each 0 or 1), sets
+ * the absolute sweep index, recounts n_unlike and n_A, and zeroes the counters.
+ * Restoring a lattice saved with klmc_get_lattice at sweep s and continuing
+ * reproduces the uninterrupted run exactly. */
+klmc_status klmc_set_lattice(klmc_ctx *c, const uint8_t *host_in, int64_t n, int64_t sweep_index);
+
+/* Lattice sides, geometry and n_A of a handle.  Any pointer may be NULL. */
+klmc_status klmc_get_shape(klmc_ctx *c, int32_t *Lx, int32_t *Ly, int32_t *geometry, int64_t *n_A);
+
+/* Waits for all work enqueued on the handle's stream. */
+klmc_status klmc_synchronize(klmc_ctx *c);
+
+/* Frees a handle created by klmc_create/klmc_create_ex.  NULL is accepted.
+ * ESTATE for a replica view obtained from klmc_batch_replica. */
+klmc_status klmc_destroy(klmc_ctx *c);
+
+/* Batched form: n independent replicas (own sizes, compositions, omega, seeds)
+ * advanced together by one launch of the resident kernel, one CTA per replica.
+ * All replicas use the stream of reps[0]. */
+klmc_status klmc_batch_create(klmc_batch **out, const klmc_params *reps, int32_t n);
+
+/* Enqueues n_mcs[i] steps for replica i (entries may differ; 0 skips). */
+klmc_status klmc_batch_sweep(klmc_batch *b, const int64_t *n_mcs);
+
+/* Borrowed handle of replica i, usable with every per-lattice call except
+ * klmc_destroy; valid until klmc_batch_destroy. */
+klmc_status klmc_batch_replica(klmc_batch *b, int32_t i, klmc_ctx **view);
+
+/* Frees the batch and its replicas.  NULL is accepted. */
+klmc_status klmc_batch_destroy(klmc_batch *b);
+
+/* Human-readable name of a status. */
+const char *klmc_status_str(klmc_status s);
+
+/* Message describing the last error on the calling thread ("" if none). */
+const char *klmc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KLMC_H */

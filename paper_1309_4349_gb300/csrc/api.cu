@@ -1,0 +1,585 @@
+// api.cu -- host runtime behind the C ABI in include/klmc.h: handle lifetime,
+// device memory, the FP64 acceptance-threshold table, and the launches.
+#include <math.h>
+#include <string.h>
+
+#include <new>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "klmc.h"
+#include "klmc_internal.h"
+
+using namespace klmc;
+
+namespace {
+
+thread_local std::string g_err;
+
+klmc_status fail(klmc_status s, const std::string &msg)
+{
+    g_err = msg;
+    return s;
+}
+
+#define KLMC_CUDA(expr)                                                                            \
+    do {                                                                                           \
+        cudaError_t e_ = (expr);                                                                   \
+        if (e_ != cudaSuccess)                                                                     \
+            return fail(KLMC_ECUDA, std::string(#expr) + ": " + cudaGetErrorString(e_));           \
+    } while (0)
+
+bool device_ok(std::string *why)
+{
+    int dev = 0, n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || n == 0) {
+        *why = "no CUDA device";
+        return false;
+    }
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        *why = "cudaGetDevice failed";
+        return false;
+    }
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) {
+        *why = "cudaGetDeviceProperties failed";
+        return false;
+    }
+    if (prop.major * 10 + prop.minor != 103) {
+        *why = "library built for sm_103a; device is sm_" + std::to_string(prop.major * 10 + prop.minor);
+        return false;
+    }
+    return true;
+}
+
+}  // namespace
+
+struct klmc_ctx {
+    klmc_params p;
+    long long N = 0, nA = 0;
+    int W = 0, pitch = 0;
+    size_t lat_bytes = 0;
+    void *lat = nullptr;
+    long long *state = nullptr;   // StateSlot array
+    void *init_scratch = nullptr;
+    long long sweep = 0;
+    SweepJob job;                 // host copy of the static job
+    cudaStream_t stream = nullptr;
+    void *cluster_mem = nullptr;  // lazily: ClusterScratch + host-API output
+    ClusterScratch cs;
+    long long *hist_out = nullptr;
+    long long hist_cap = 0;
+    uint8_t *dbytes = nullptr;    // lazily: one byte per site
+    klmc_batch *owner = nullptr;  // non-null for replica views
+    std::vector<std::pair<void *, size_t>> allocs;
+};
+
+struct klmc_batch {
+    std::vector<klmc_ctx *> reps;
+    SweepJob *djobs = nullptr;
+    SweepCall *dcalls = nullptr;
+    std::vector<SweepCall> hcalls;
+    cudaStream_t stream = nullptr;
+    klmc_ctx *mem_owner = nullptr;  // holds the batch arrays' allocations
+};
+
+namespace {
+
+void *dev_alloc(klmc_ctx *c, size_t bytes)
+{
+    void *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    if (c->p.alloc) {
+        p = c->p.alloc(bytes, c->p.stream, c->p.user);
+    } else if (cudaMallocAsync(&p, bytes, c->stream) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    if (p) c->allocs.push_back({p, bytes});
+    return p;
+}
+
+void free_all(klmc_ctx *c)
+{
+    for (auto &a : c->allocs) {
+        if (c->p.alloc && c->p.free) c->p.free(a.first, a.second, c->p.stream, c->p.user);
+        else if (!c->p.alloc) cudaFreeAsync(a.first, c->stream);
+    }
+    c->allocs.clear();
+    cudaStreamSynchronize(c->stream);
+}
+
+klmc_status validate(const klmc_params *p)
+{
+    if (!p) return fail(KLMC_EINVAL, "params is NULL");
+    if (p->Lx < 4 || p->Ly < 4) return fail(KLMC_EINVAL, "Lx and Ly must be >= 4");
+    const long long N = (long long)p->Lx * p->Ly;
+    if (N > 2147483647LL) return fail(KLMC_EINVAL, "Lx*Ly must be <= 2^31 - 1");
+    if (p->geometry != KLMC_TRI6 && p->geometry != KLMC_SQ4) return fail(KLMC_EINVAL, "unknown geometry");
+    if (p->boundary != KLMC_PERIODIC) return fail(KLMC_EINVAL, "only periodic boundaries are supported");
+    if (p->packing != KLMC_PACK_AUTO && p->packing != KLMC_PACK_BIT && p->packing != KLMC_PACK_BYTE)
+        return fail(KLMC_EINVAL, "unknown packing");
+    if (!isfinite(p->omega_over_kT)) return fail(KLMC_EINVAL, "omega_over_kT must be finite");
+    if (p->n_A < 0 && !(p->fraction_A >= 0.0 && p->fraction_A <= 1.0))
+        return fail(KLMC_EINVAL, "fraction_A must be in [0, 1]");
+    if (p->n_A > N) return fail(KLMC_EINVAL, "n_A must be in [0, Lx*Ly]");
+    if (p->alloc && !p->free) return fail(KLMC_EINVAL, "alloc given without free");
+    return KLMC_OK;
+}
+
+// Acceptance table (Metropolis step c with u = r / 2^32): a pair whose
+// neighbour-agreement sum is S changes n_unlike by dn = 2 (S - (z - 1)); it is
+// accepted without a draw when (omega/kT) dn <= 0, otherwise iff a 32-bit draw
+// r < ceil(exp(-(omega/kT) dn) 2^32).  Built once, in FP64, on the host.
+klmc_status build_thresholds(double bw, int geometry, SweepJob *J)
+{
+    const int zm1 = (geometry == KLMC_TRI6 ? 6 : 4) - 1;
+    int lo = 16, hi = -1;
+    for (int S = 0; S < 16; ++S) J->thr[S] = 0;
+    for (int S = 0; S <= 2 * zm1; ++S) {
+        const int dn = 2 * (S - zm1);
+        const double x = bw * (double)dn;
+        if (x <= 0.0) continue;
+        J->thr[S] = (uint64_t)ceil(ldexp(exp(-x), 32));
+        if (S < lo) lo = S;
+        if (S > hi) hi = S;
+    }
+    for (int S = lo; S <= hi; ++S) {
+        const double x = bw * (double)(2 * (S - zm1));
+        if (x <= 0.0) return fail(KLMC_EINVAL, "internal: draw set is not an interval");
+    }
+    if (hi < 0) {
+        lo = 1;
+        hi = 0;
+    }
+    J->draw_lo = lo;
+    J->draw_hi = hi;
+    return KLMC_OK;
+}
+
+klmc_status ensure_bytes(klmc_ctx *c)
+{
+    if (c->dbytes) return KLMC_OK;
+    c->dbytes = (uint8_t *)dev_alloc(c, (size_t)c->N);
+    if (!c->dbytes) return fail(KLMC_ENOMEM, "device allocation of the byte lattice failed");
+    return KLMC_OK;
+}
+
+klmc_status ensure_clusters(klmc_ctx *c)
+{
+    if (c->cluster_mem) return KLMC_OK;
+    const long long nsp = c->N;
+    long long cap = (long long)floor(sqrt(2.0 * (double)c->N)) + 2;
+    const size_t sbytes = cluster_scratch_bytes(c->N, nsp);
+    const size_t obytes = (size_t)(2 * cap + 2) * sizeof(long long);
+    void *mem = dev_alloc(c, sbytes + obytes);
+    if (!mem) return fail(KLMC_ENOMEM, "device allocation of cluster scratch failed");
+    cluster_scratch_carve(mem, c->N, nsp, &c->cs);
+    KLMC_CUDA(cluster_scratch_clear(c->cs, c->stream));
+    c->cluster_mem = mem;
+    c->hist_out = (long long *)((char *)mem + sbytes);
+    c->hist_cap = cap;
+    return KLMC_OK;
+}
+
+klmc_status create_one(klmc_ctx **out, const klmc_params *p, klmc_batch *owner)
+{
+    klmc_status st = validate(p);
+    if (st != KLMC_OK) return st;
+    std::string why;
+    if (!device_ok(&why)) return fail(KLMC_ENODEV, why);
+    klmc_ctx *c = new (std::nothrow) klmc_ctx();
+    if (!c) return fail(KLMC_ENOMEM, "host allocation failed");
+    c->p = *p;
+    if (c->p.packing == KLMC_PACK_AUTO) c->p.packing = KLMC_PACK_BIT;
+    c->owner = owner;
+    c->stream = (cudaStream_t)p->stream;
+    c->N = (long long)p->Lx * p->Ly;
+    c->nA = p->n_A >= 0 ? p->n_A : (long long)floor(p->fraction_A * (double)c->N + 0.5);
+    c->W = (p->Lx + 31) / 32;
+    if (c->p.packing == KLMC_PACK_BIT) {
+        c->pitch = (c->W + 3) / 4 * 4;  // 16-byte rows
+        c->lat_bytes = (size_t)c->pitch * 4 * p->Ly;
+    } else {
+        c->pitch = (p->Lx + 15) / 16 * 16;
+        c->lat_bytes = (size_t)c->pitch * p->Ly;
+    }
+    c->lat = dev_alloc(c, c->lat_bytes);
+    c->state = (long long *)dev_alloc(c, kStateSlots * sizeof(long long));
+    c->init_scratch = dev_alloc(c, init_scratch_bytes());
+    if (!c->lat || !c->state || !c->init_scratch) {
+        free_all(c);
+        delete c;
+        return fail(KLMC_ENOMEM, "device allocation failed");
+    }
+    SweepJob &J = c->job;
+    memset(&J, 0, sizeof(J));
+    J.lat = c->lat;
+    J.Lx = p->Lx;
+    J.Ly = p->Ly;
+    J.pitch = c->pitch;
+    J.packing = c->p.packing;
+    J.geometry = p->geometry;
+    J.W = c->W;
+    J.RW = (p->Lx + 127) / 32;
+    J.magicW = (0x100000000ull + (unsigned long long)c->W - 1) / (unsigned long long)c->W;
+    J.key0 = (uint32_t)p->seed;
+    J.key1 = (uint32_t)(p->seed >> 32);
+    J.state = c->state;
+    st = build_thresholds(p->omega_over_kT, p->geometry, &J);
+    if (st != KLMC_OK) {
+        free_all(c);
+        delete c;
+        return st;
+    }
+    cudaError_t e = cudaMemsetAsync(c->state, 0, kStateSlots * sizeof(long long), c->stream);
+    if (e == cudaSuccess)
+        e = launch_init_lattice(c->lat, J.packing, p->Lx, p->Ly, c->pitch, J.key0, J.key1, c->nA,
+                                c->init_scratch, c->stream);
+    if (e == cudaSuccess)
+        e = launch_recount(c->lat, J.packing, p->Lx, p->Ly, c->pitch, p->geometry,
+                           c->state + kNUnlike, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        free_all(c);
+        delete c;
+        return fail(KLMC_ECUDA, std::string("create: ") + cudaGetErrorString(e));
+    }
+    *out = c;
+    return KLMC_OK;
+}
+
+klmc_status check_resident(const klmc_ctx *c)
+{
+    if (resident_smem_bytes(c->p.Lx, c->p.Ly) > (size_t)resident_max_smem_bytes())
+        return fail(KLMC_EINVAL, "lattice too large for the shared-memory resident sweep (" +
+                                     std::to_string(resident_smem_bytes(c->p.Lx, c->p.Ly)) +
+                                     " bytes of padded bit rows)");
+    return KLMC_OK;
+}
+
+klmc_status sweep_one(klmc_ctx *c, int64_t n_mcs, int64_t trace_every, int64_t *dev_trace)
+{
+    if (!c) return fail(KLMC_EINVAL, "ctx is NULL");
+    if (n_mcs < 0) return fail(KLMC_EINVAL, "n_mcs must be >= 0");
+    if (trace_every < 0 || (trace_every > 0 && !dev_trace))
+        return fail(KLMC_EINVAL, "trace_every > 0 needs a device trace buffer");
+    if (n_mcs == 0) return KLMC_OK;
+    klmc_status st = check_resident(c);
+    if (st != KLMC_OK) return st;
+    SweepCall call;
+    call.sweep0 = c->sweep;
+    call.n_mcs = n_mcs;
+    call.trace = (long long *)dev_trace;
+    call.trace_every = trace_every;
+    KLMC_CUDA(launch_resident_sweep_one(c->job, call, resident_smem_bytes(c->p.Lx, c->p.Ly),
+                                        c->stream));
+    c->sweep += n_mcs;
+    return KLMC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+klmc_status klmc_params_default(klmc_params *p)
+{
+    if (!p) return fail(KLMC_EINVAL, "params is NULL");
+    memset(p, 0, sizeof(*p));
+    p->Lx = p->Ly = 64;
+    p->geometry = KLMC_TRI6;
+    p->boundary = KLMC_PERIODIC;
+    p->packing = KLMC_PACK_BIT;
+    p->n_A = -1;
+    p->fraction_A = 0.5;
+    p->omega_over_kT = 0.0;
+    p->seed = 1;
+    return KLMC_OK;
+}
+
+klmc_status klmc_create(klmc_ctx **out, int32_t L, double composition_A, double omega_over_kT,
+                        uint64_t seed)
+{
+    if (!out) return fail(KLMC_EINVAL, "out is NULL");
+    klmc_params p;
+    klmc_params_default(&p);
+    p.Lx = p.Ly = L;
+    p.fraction_A = composition_A;
+    p.omega_over_kT = omega_over_kT;
+    p.seed = seed;
+    return create_one(out, &p, nullptr);
+}
+
+klmc_status klmc_create_ex(klmc_ctx **out, const klmc_params *p)
+{
+    if (!out) return fail(KLMC_EINVAL, "out is NULL");
+    return create_one(out, p, nullptr);
+}
+
+klmc_status klmc_sweep(klmc_ctx *c, int64_t n_mcs) { return sweep_one(c, n_mcs, 0, nullptr); }
+
+klmc_status klmc_sweep_traced(klmc_ctx *c, int64_t n_mcs, int64_t trace_every, int64_t *dev_trace)
+{
+    if (trace_every <= 0) return fail(KLMC_EINVAL, "trace_every must be > 0");
+    return sweep_one(c, n_mcs, trace_every, dev_trace);
+}
+
+klmc_status klmc_energy(klmc_ctx *c, int64_t *n_unlike, double *energy_over_kT)
+{
+    if (!c) return fail(KLMC_EINVAL, "ctx is NULL");
+    long long v = 0;
+    KLMC_CUDA(cudaMemcpyAsync(&v, c->state + kNUnlike, sizeof(v), cudaMemcpyDeviceToHost, c->stream));
+    KLMC_CUDA(cudaStreamSynchronize(c->stream));
+    if (n_unlike) *n_unlike = v;
+    if (energy_over_kT) *energy_over_kT = c->p.omega_over_kT * (double)v;
+    return KLMC_OK;
+}
+
+klmc_status klmc_energy_recount(klmc_ctx *c, int64_t *n_unlike)
+{
+    if (!c || !n_unlike) return fail(KLMC_EINVAL, "NULL argument");
+    KLMC_CUDA(launch_recount(c->lat, c->job.packing, c->p.Lx, c->p.Ly, c->pitch, c->p.geometry,
+                             c->state + kScratch0, c->stream));
+    long long v = 0;
+    KLMC_CUDA(cudaMemcpyAsync(&v, c->state + kScratch0, sizeof(v), cudaMemcpyDeviceToHost, c->stream));
+    KLMC_CUDA(cudaStreamSynchronize(c->stream));
+    *n_unlike = v;
+    return KLMC_OK;
+}
+
+klmc_status klmc_cluster_histogram_device(klmc_ctx *c, int32_t species, int64_t *dev_sizes,
+                                          int64_t *dev_counts, int64_t capacity,
+                                          int64_t *dev_n_distinct)
+{
+    if (!c || !dev_n_distinct) return fail(KLMC_EINVAL, "NULL argument");
+    if (species != 0 && species != 1) return fail(KLMC_EINVAL, "species must be 0 (B) or 1 (A)");
+    if (capacity < 0 || (capacity > 0 && (!dev_sizes || !dev_counts)))
+        return fail(KLMC_EINVAL, "bad output buffers");
+    klmc_status st = ensure_clusters(c);
+    if (st != KLMC_OK) return st;
+    KLMC_CUDA(launch_cluster_histogram(c->lat, c->job.packing, c->p.Lx, c->p.Ly, c->pitch,
+                                       c->p.geometry, species, c->cs, (long long *)dev_sizes,
+                                       (long long *)dev_counts, capacity,
+                                       (long long *)dev_n_distinct, c->stream));
+    return KLMC_OK;
+}
+
+klmc_status klmc_cluster_histogram(klmc_ctx *c, int32_t species, int64_t *sizes, int64_t *counts,
+                                   int64_t capacity, int64_t *n_distinct)
+{
+    if (!c || !n_distinct) return fail(KLMC_EINVAL, "NULL argument");
+    if (capacity < 0 || (capacity > 0 && (!sizes || !counts)))
+        return fail(KLMC_EINVAL, "bad output buffers");
+    klmc_status st = ensure_clusters(c);
+    if (st != KLMC_OK) return st;
+    long long *dsz = c->hist_out, *dct = c->hist_out + c->hist_cap, *dn = c->hist_out + 2 * c->hist_cap;
+    st = klmc_cluster_histogram_device(c, species, (int64_t *)dsz, (int64_t *)dct, c->hist_cap,
+                                       (int64_t *)dn);
+    if (st != KLMC_OK) return st;
+    long long n = 0;
+    KLMC_CUDA(cudaMemcpyAsync(&n, dn, sizeof(n), cudaMemcpyDeviceToHost, c->stream));
+    KLMC_CUDA(cudaStreamSynchronize(c->stream));
+    if (n > c->hist_cap) return fail(KLMC_ECUDA, "internal: more distinct sizes than the bound");
+    if (n > capacity) {
+        *n_distinct = n;
+        return fail(KLMC_ETRUNC, "capacity " + std::to_string(capacity) + " < " + std::to_string(n));
+    }
+    if (n > 0) {
+        KLMC_CUDA(cudaMemcpyAsync(sizes, dsz, (size_t)n * 8, cudaMemcpyDeviceToHost, c->stream));
+        KLMC_CUDA(cudaMemcpyAsync(counts, dct, (size_t)n * 8, cudaMemcpyDeviceToHost, c->stream));
+        KLMC_CUDA(cudaStreamSynchronize(c->stream));
+    }
+    *n_distinct = n;
+    return KLMC_OK;
+}
+
+klmc_status klmc_get_counters(klmc_ctx *c, klmc_counters *out)
+{
+    if (!c || !out) return fail(KLMC_EINVAL, "NULL argument");
+    long long v[kStateSlots];
+    KLMC_CUDA(cudaMemcpyAsync(v, c->state, sizeof(v), cudaMemcpyDeviceToHost, c->stream));
+    KLMC_CUDA(cudaStreamSynchronize(c->stream));
+    out->sweeps = c->sweep;
+    out->attempts = v[kAttempts];
+    out->unlike = v[kUnlike];
+    out->draws = v[kDraws];
+    out->accepts = v[kAccepts];
+    return KLMC_OK;
+}
+
+klmc_status klmc_get_lattice(klmc_ctx *c, uint8_t *host_out, int64_t n)
+{
+    if (!c || !host_out) return fail(KLMC_EINVAL, "NULL argument");
+    if (n != c->N) return fail(KLMC_EINVAL, "n must equal Lx*Ly");
+    klmc_status st = ensure_bytes(c);
+    if (st != KLMC_OK) return st;
+    KLMC_CUDA(launch_unpack(c->lat, c->job.packing, c->p.Lx, c->p.Ly, c->pitch, c->dbytes, c->stream));
+    KLMC_CUDA(cudaMemcpyAsync(host_out, c->dbytes, (size_t)n, cudaMemcpyDeviceToHost, c->stream));
+    KLMC_CUDA(cudaStreamSynchronize(c->stream));
+    return KLMC_OK;
+}
+
+klmc_status klmc_set_lattice(klmc_ctx *c, const uint8_t *host_in, int64_t n, int64_t sweep_index)
+{
+    if (!c || !host_in) return fail(KLMC_EINVAL, "NULL argument");
+    if (n != c->N) return fail(KLMC_EINVAL, "n must equal Lx*Ly");
+    if (sweep_index < 0) return fail(KLMC_EINVAL, "sweep_index must be >= 0");
+    for (long long i = 0; i < n; ++i)
+        if (host_in[i] > 1) return fail(KLMC_EINVAL, "lattice bytes must be 0 or 1");
+    klmc_status st = ensure_bytes(c);
+    if (st != KLMC_OK) return st;
+    KLMC_CUDA(cudaMemcpyAsync(c->dbytes, host_in, (size_t)n, cudaMemcpyHostToDevice, c->stream));
+    KLMC_CUDA(launch_pack(c->dbytes, c->lat, c->job.packing, c->p.Lx, c->p.Ly, c->pitch, c->stream));
+    KLMC_CUDA(cudaMemsetAsync(c->state, 0, kStateSlots * sizeof(long long), c->stream));
+    KLMC_CUDA(launch_recount(c->lat, c->job.packing, c->p.Lx, c->p.Ly, c->pitch, c->p.geometry,
+                             c->state + kNUnlike, c->stream));
+    KLMC_CUDA(launch_count_A(c->lat, c->job.packing, c->p.Lx, c->p.Ly, c->pitch, c->state + kScratch0,
+                             c->stream));
+    long long nA = 0;
+    KLMC_CUDA(cudaMemcpyAsync(&nA, c->state + kScratch0, sizeof(nA), cudaMemcpyDeviceToHost, c->stream));
+    KLMC_CUDA(cudaStreamSynchronize(c->stream));
+    c->nA = nA;
+    c->sweep = sweep_index;
+    return KLMC_OK;
+}
+
+klmc_status klmc_get_shape(klmc_ctx *c, int32_t *Lx, int32_t *Ly, int32_t *geometry, int64_t *n_A)
+{
+    if (!c) return fail(KLMC_EINVAL, "ctx is NULL");
+    if (Lx) *Lx = c->p.Lx;
+    if (Ly) *Ly = c->p.Ly;
+    if (geometry) *geometry = c->p.geometry;
+    if (n_A) *n_A = c->nA;
+    return KLMC_OK;
+}
+
+klmc_status klmc_synchronize(klmc_ctx *c)
+{
+    if (!c) return fail(KLMC_EINVAL, "ctx is NULL");
+    KLMC_CUDA(cudaStreamSynchronize(c->stream));
+    return KLMC_OK;
+}
+
+klmc_status klmc_destroy(klmc_ctx *c)
+{
+    if (!c) return KLMC_OK;
+    if (c->owner) return fail(KLMC_ESTATE, "replica views are freed by klmc_batch_destroy");
+    free_all(c);
+    delete c;
+    return KLMC_OK;
+}
+
+klmc_status klmc_batch_create(klmc_batch **out, const klmc_params *reps, int32_t n)
+{
+    if (!out || !reps || n <= 0) return fail(KLMC_EINVAL, "bad batch arguments");
+    klmc_batch *b = new (std::nothrow) klmc_batch();
+    if (!b) return fail(KLMC_ENOMEM, "host allocation failed");
+    b->stream = (cudaStream_t)reps[0].stream;
+    for (int i = 0; i < n; ++i) {
+        klmc_params p = reps[i];
+        p.stream = reps[0].stream;
+        klmc_ctx *c = nullptr;
+        klmc_status st = create_one(&c, &p, b);
+        if (st == KLMC_OK) st = check_resident(c);
+        if (st != KLMC_OK) {
+            std::string msg = "replica " + std::to_string(i) + ": " + g_err;
+            if (c) {
+                c->owner = nullptr;
+                klmc_destroy(c);
+            }
+            klmc_batch_destroy(b);
+            return fail(st, msg);
+        }
+        b->reps.push_back(c);
+    }
+    klmc_ctx *m = b->reps[0];
+    b->mem_owner = m;
+    b->djobs = (SweepJob *)dev_alloc(m, sizeof(SweepJob) * (size_t)n);
+    b->dcalls = (SweepCall *)dev_alloc(m, sizeof(SweepCall) * (size_t)n);
+    if (!b->djobs || !b->dcalls) {
+        klmc_batch_destroy(b);
+        return fail(KLMC_ENOMEM, "device allocation of the batch tables failed");
+    }
+    std::vector<SweepJob> jobs(n);
+    for (int i = 0; i < n; ++i) jobs[i] = b->reps[i]->job;
+    cudaError_t e = cudaMemcpyAsync(b->djobs, jobs.data(), sizeof(SweepJob) * (size_t)n,
+                                    cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) {
+        klmc_batch_destroy(b);
+        return fail(KLMC_ECUDA, std::string("batch upload: ") + cudaGetErrorString(e));
+    }
+    b->hcalls.resize(n);
+    *out = b;
+    return KLMC_OK;
+}
+
+klmc_status klmc_batch_sweep(klmc_batch *b, const int64_t *n_mcs)
+{
+    if (!b || !n_mcs) return fail(KLMC_EINVAL, "NULL argument");
+    const int n = (int)b->reps.size();
+    size_t smem = 0;
+    bool any = false;
+    for (int i = 0; i < n; ++i) {
+        if (n_mcs[i] < 0) return fail(KLMC_EINVAL, "n_mcs entries must be >= 0");
+        klmc_ctx *c = b->reps[i];
+        SweepCall &call = b->hcalls[i];
+        call.sweep0 = c->sweep;
+        call.n_mcs = n_mcs[i];
+        call.trace = nullptr;
+        call.trace_every = 0;
+        if (n_mcs[i] > 0) {
+            any = true;
+            const size_t s = resident_smem_bytes(c->p.Lx, c->p.Ly);
+            if (s > smem) smem = s;
+        }
+    }
+    if (!any) return KLMC_OK;
+    KLMC_CUDA(cudaMemcpyAsync(b->dcalls, b->hcalls.data(), sizeof(SweepCall) * (size_t)n,
+                              cudaMemcpyHostToDevice, b->stream));
+    KLMC_CUDA(launch_resident_sweep(b->djobs, b->dcalls, n, smem, b->stream));
+    for (int i = 0; i < n; ++i) b->reps[i]->sweep += n_mcs[i];
+    return KLMC_OK;
+}
+
+klmc_status klmc_batch_replica(klmc_batch *b, int32_t i, klmc_ctx **view)
+{
+    if (!b || !view) return fail(KLMC_EINVAL, "NULL argument");
+    if (i < 0 || i >= (int32_t)b->reps.size()) return fail(KLMC_EINVAL, "replica index out of range");
+    *view = b->reps[i];
+    return KLMC_OK;
+}
+
+klmc_status klmc_batch_destroy(klmc_batch *b)
+{
+    if (!b) return KLMC_OK;
+    // The batch tables were allocated on reps[0]; free them with it, last.
+    for (size_t i = b->reps.size(); i-- > 0;) {
+        klmc_ctx *c = b->reps[i];
+        free_all(c);
+        delete c;
+    }
+    delete b;
+    return KLMC_OK;
+}
+
+const char *klmc_status_str(klmc_status s)
+{
+    switch (s) {
+    case KLMC_OK: return "KLMC_OK";
+    case KLMC_EINVAL: return "KLMC_EINVAL";
+    case KLMC_ENOMEM: return "KLMC_ENOMEM";
+    case KLMC_ECUDA: return "KLMC_ECUDA";
+    case KLMC_ETIMEOUT: return "KLMC_ETIMEOUT";
+    case KLMC_EBUSY: return "KLMC_EBUSY";
+    case KLMC_ETRUNC: return "KLMC_ETRUNC";
+    case KLMC_ESTATE: return "KLMC_ESTATE";
+    case KLMC_ENODEV: return "KLMC_ENODEV";
+    }
+    return "KLMC_UNKNOWN";
+}
+
+const char *klmc_last_error(void) { return g_err.c_str(); }
+
+}  // extern "C"

