@@ -1,0 +1,424 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the Kawasaki lattice Monte Carlo hot path.
+
+Workload (the paper's 400x400 lattice size, section "Cluster Analysis"): five
+separate runs of a 400x400 periodic triangular lattice with 30 % A / 70 % B
+placed at random, omega/kT in {0.2, 0.4, 0.6, 0.8, 1.0} (seeds 2..6), 20000
+Monte Carlo steps each, the A-cluster size histogram every 500 steps, lattice
+stored at 1 bit per site.  Inputs are synthetic, seeded random lattices.
+
+One benchmark step = the whole workload: load the five initial lattices, run
+20000 steps of each with the 40 histograms each.  Metric: Kawasaki exchange
+attempts per second (attempts are counted exactly by the kernels).
+
+Forms: "batched" (one resident-kernel launch advances all five lattices, one
+CTA each; this is ``value``) and "plain" (one launch per lattice, issued in
+turn).  ``e2e`` is the batched form through the public API with the initial
+lattices copied from pinned host memory and all histograms, lattices and
+energies copied back, inside the timed region.
+
+``--impl reference`` times the CPU oracle (the plain sequential C program in
+oracle/) on a bounded sample of the same workload on the host cores.
+
+Multi-GPU (torchrun): every rank runs its own independent copy of the workload
+(seeds offset by rank), no collective on the data path; weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+L = 400
+FRACTION_A = 0.3
+OMEGAS = [0.2, 0.4, 0.6, 0.8, 1.0]
+SEEDS = [2, 3, 4, 5, 6]
+N_MCS = 20000
+HIST_EVERY = 500
+WORKLOAD = ("400x400 TRI6 periodic, 30% A random start, omega/kT in {0.2,0.4,0.6,0.8,1.0} "
+            "(5 separate runs, seeds 2..6), 20000 MCS each, A-cluster histogram every 500 MCS, "
+            "1 bit/site")
+
+# Operation model of the sweep kernel (lane-instructions per attempt), used for
+# the ALU roofline: C_PAIR is the bit-sliced neighbour evaluation of one
+# anchor word (windows, comparisons, adder tree, masks) divided by the anchors
+# per word, averaged over the three orientations; C_PHILOX is one Philox4x32-10
+# evaluation (10 rounds x (2 IMAD.WIDE + 2 LOP3)), paid only by drawn attempts.
+C_PAIR = 4.8
+C_PHILOX = 40.0
+# INT32 lanes per SM per clock: 4 sub-partitions x 16.  The probe
+# paper_1309_4349_gb300/probes/int_peak.cu measures 60 LOP3 and 30 IMAD.WIDE
+# (+30 LOP3) lane-ops/clk/SM on GB300, i.e. one 64-lane integer pipe.
+INT32_LANES_PER_SM = 64
+# Kernels launched per library call (fixed by the library's structure).
+LAUNCHES_SWEEP = 1
+LAUNCHES_HISTOGRAM = 5
+LAUNCHES_SET_LATTICE_DEVICE = 3
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--mcs", type=int, default=N_MCS, help="steps per run (default: the workload's)")
+    ap.add_argument("--skip-plain", action="store_true")
+    ap.add_argument("--skip-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def dist_info():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    QUERY = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", self.gpu_id, f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def gpu_smi_id(torch, dev: int) -> str:
+    try:
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        return str(dev)
+
+
+def oracle_sample(n_mcs: int, threads: int):
+    """The oracle on a bounded sample: each of the five runs for n_mcs steps plus
+    one cluster histogram, one host thread per run (ctypes releases the GIL)."""
+    import numpy as np  # noqa: F401
+
+    import oracle
+
+    oracle.build()
+    inits = [oracle.init(L, L, oracle.n_A(L, L, -1, FRACTION_A), s) for s in SEEDS]
+    res = [None] * len(SEEDS)
+
+    def work(i):
+        r = oracle.run(L, L, oracle.TRI6, OMEGAS[i], SEEDS[i], inits[i], 0, n_mcs)
+        oracle.cluster_histogram(L, L, oracle.TRI6, r.lattice, 1)
+        res[i] = r.attempts
+
+    t0 = time.perf_counter()
+    ths = [threading.Thread(target=work, args=(i,)) for i in range(len(SEEDS))]
+    for t in ths:
+        t.start()
+    for t in ths:
+        t.join()
+    dt = time.perf_counter() - t0
+    return sum(res), dt
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    n_mcs = 60
+    for _ in range(args.warmup):
+        oracle_sample(n_mcs, len(SEEDS))
+    att, tot = 0, 0.0
+    for _ in range(args.steps):
+        a, dt = oracle_sample(n_mcs, len(SEEDS))
+        att += a
+        tot += dt
+    value = att / tot
+    sample = (f"{n_mcs} MCS of each of the 5 runs plus one A-cluster histogram each, per step; "
+              f"one host thread per run")
+    line = {
+        "impl": "reference", "metric": "Kawasaki exchange attempts/s", "value": value,
+        "unit": "attempts/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "form": "oracle (plain sequential C, CPU)"},
+        "cpu_baseline": {"value": value, "unit": "attempts/s", "cores": len(SEEDS),
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "attempts/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_info()
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+
+    import numpy as np
+    import torch
+
+    import paper_1309_4349_gb300 as klmc
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU (the library has no CPU path)")
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    klmc.build()
+    n_mcs = args.mcs
+    n_seg = n_mcs // HIST_EVERY
+    assert n_seg * HIST_EVERY == n_mcs
+    seeds = [s + 1000 * rank for s in SEEDS]
+    reps = [dict(Lx=L, Ly=L, fraction_A=FRACTION_A, omega_over_kT=w, seed=s,
+                 packing=klmc.PACK_BIT) for w, s in zip(OMEGAS, seeds)]
+    nrun = len(reps)
+    N = L * L
+    stream = torch.cuda.current_stream()
+
+    batch = klmc.Batch(reps)
+    init_host = [batch.replicas[i].get_lattice() for i in range(nrun)]
+    init_dev = [torch.from_numpy(t).cuda() for t in init_host]
+    hcap = int(np.sqrt(2.0 * N)) + 2
+    sizes = torch.zeros((nrun, n_seg, hcap), dtype=torch.int64, device="cuda")
+    counts = torch.zeros_like(sizes)
+    ndist = torch.zeros((nrun, n_seg), dtype=torch.int64, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    sweep_events = []
+
+    def histograms(lats, seg):
+        for i, lat in enumerate(lats):
+            lat.cluster_histogram_device(1, sizes[i, seg], counts[i, seg], ndist[i, seg:seg + 1])
+
+    def step_batched(record=False):
+        for i, lat in enumerate(batch.replicas):
+            lat.set_lattice_device(init_dev[i], 0)
+        for seg in range(n_seg):
+            if record:
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+            batch.sweep(HIST_EVERY)
+            if record:
+                e1.record(stream)
+                sweep_events.append((e0, e1))
+            histograms(batch.replicas, seg)
+
+    plain = [batch.replicas[i] for i in range(nrun)]
+
+    def step_plain():
+        for i, lat in enumerate(plain):
+            lat.set_lattice_device(init_dev[i], 0)
+        for seg in range(n_seg):
+            for lat in plain:
+                lat.sweep(HIST_EVERY)
+            histograms(plain, seg)
+
+    def timed(step, K, W, record=False):
+        for _ in range(W):
+            step()
+        torch.cuda.synchronize()
+        barrier()
+        evs = []
+        for _ in range(K):
+            flush.zero_()  # L2 (129 MB) flushed between steps, outside the timed events
+            s = torch.cuda.Event(enable_timing=True)
+            e = torch.cuda.Event(enable_timing=True)
+            s.record(stream)
+            if record:
+                step(record=True)
+            else:
+                step()
+            e.record(stream)
+            evs.append((s, e))
+        torch.cuda.synchronize()
+        barrier()
+        return [s.elapsed_time(e) for s, e in evs]
+
+    # ---------------- batched (the reported value) ----------------
+    clocks = ClockSampler(gpu_smi_id(torch, local))
+    clocks.start()
+    ms_steps = timed(step_batched, args.steps, args.warmup, record=True)
+    clk = clocks.stop()
+    ms_step = sum(ms_steps) / len(ms_steps)
+    cnt = [lat.counters() for lat in batch.replicas]
+    attempts_step = sum(c["attempts"] for c in cnt)
+    draws_step = sum(c["draws"] for c in cnt)
+    assert attempts_step == nrun * n_mcs * N, attempts_step  # 4 | 400: N attempts per MCS
+    # max over ranks of the device time
+    t = torch.tensor([ms_step], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_step_max = float(t.item())
+    value = world * attempts_step / (ms_step_max * 1e-3)
+
+    sweep_ms = [e0.elapsed_time(e1) for e0, e1 in sweep_events]
+    launch_ms = sum(sweep_ms) / len(sweep_ms)
+    attempts_launch = nrun * HIST_EVERY * N
+    p_draw = draws_step / attempts_step
+    ops_attempt = C_PAIR + p_draw * C_PHILOX
+    sm_count = torch.cuda.get_device_properties(local).multi_processor_count
+    sm_mhz = clk["sm_mhz"] if clk else 2070.0
+    peak_tops = sm_count * INT32_LANES_PER_SM * sm_mhz * 1e6 / 1e12
+    achieved_tops = ops_attempt * attempts_launch / (launch_ms * 1e-3) / 1e12
+    cluster, threads = batch.replicas[0].launch_shape()
+    ctas = nrun * cluster
+    roofline = {"bound": "alu", "kernel": "resident_sweep_kernel", "achieved": achieved_tops,
+                "peak": peak_tops, "unit": "Tops/s (INT32 lane-ops)", "frac": achieved_tops / peak_tops,
+                "traffic": None, "ops_per_attempt": ops_attempt, "p_draw": p_draw,
+                "launch_ms": launch_ms, "attempts_per_launch": attempts_launch,
+                "ctas_per_launch": ctas, "cluster": cluster, "threads_per_cta": threads,
+                "sm_count": sm_count,
+                "peak_basis": (f"{sm_count} SMs x {INT32_LANES_PER_SM} INT32 lanes/clk x median SM "
+                               f"clock {sm_mhz:.0f} MHz (derived; probes/int_peak.cu)"),
+                "frac_of_occupied_sms": achieved_tops / (peak_tops * min(ctas, sm_count) / sm_count),
+                "sweep_share_of_step": sum(sweep_ms) / sum(ms_steps)}
+
+    # Exactness spot check of the timed state (the parity tests do the full check).
+    e_run = [lat.energy()[0] for lat in batch.replicas]
+    e_rec = [lat.energy_recount() for lat in batch.replicas]
+    assert e_run == e_rec
+
+    # ---------------- plain ----------------
+    forms = {"batched": {"value": value, "ms_per_step": ms_step_max, "launches_per_step":
+                         n_seg * LAUNCHES_SWEEP}}
+    if not args.skip_plain:
+        ms_plain = timed(step_plain, 1, 1)
+        forms["plain"] = {"value": world * attempts_step / (ms_plain[0] * 1e-3),
+                          "ms_per_step": ms_plain[0], "launches_per_step": n_seg * nrun}
+
+    # ---------------- end to end through the public API, host buffers ----------------
+    pinned = [torch.from_numpy(t).pin_memory() for t in init_host]
+    pinned_np = [p.numpy() for p in pinned]
+    out_lat = [np.zeros(N, dtype=np.uint8) for _ in range(nrun)]
+
+    def step_e2e():
+        for i, lat in enumerate(batch.replicas):
+            lat.set_lattice(pinned_np[i], 0)
+        for seg in range(n_seg):
+            batch.sweep(HIST_EVERY)
+            histograms(batch.replicas, seg)
+        h = (sizes.cpu(), counts.cpu(), ndist.cpu())
+        energies = [lat.energy()[0] for lat in batch.replicas]
+        for i, lat in enumerate(batch.replicas):
+            out_lat[i][:] = lat.get_lattice()
+        return h, energies
+
+    for _ in range(args.warmup):
+        step_e2e()
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step_e2e()
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    e2e_s = float(t.item())
+    h2d = nrun * N
+    d2h = sizes.numel() * 8 + counts.numel() * 8 + ndist.numel() * 8 + nrun * N + nrun * 8
+    e2e = {"value": world * attempts_step / e2e_s, "unit": "attempts/s", "h2d_bytes_per_step": h2d,
+           "d2h_bytes_per_step": d2h, "ms_per_step": e2e_s * 1e3}
+
+    launches_step = (nrun * LAUNCHES_SET_LATTICE_DEVICE + n_seg * LAUNCHES_SWEEP +
+                     n_seg * nrun * LAUNCHES_HISTOGRAM)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.skip_cpu:
+        n_sample = 300
+        att, dt = oracle_sample(n_sample, len(SEEDS))
+        cpu = {"value": att / dt, "unit": "attempts/s", "cores": len(SEEDS), "kind": "oracle",
+               "sample": f"{n_sample} MCS of each of the 5 runs plus one A-cluster histogram each "
+                         f"({att} attempts), one host thread per run; nproc={os.cpu_count()}"}
+
+    line = {
+        "metric": "Kawasaki exchange attempts/s", "value": value, "unit": "attempts/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step_max,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD,
+                   "form": "batched (one resident launch, one thread-block cluster per lattice)",
+                   "L": L, "runs": nrun, "mcs": n_mcs, "hist_every": HIST_EVERY,
+                   "parallelism": f"replicas x{world}",
+                   "l2": "flushed between steps (256 MiB write outside the timed events)"},
+        "sites_per_s": value,  # one attempt per site per MCS: sites x MCS / s
+        "forms": forms,
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": launches_step * args.steps,
+        "clocks": clk,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    batch.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

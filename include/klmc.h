@@ -61,7 +61,8 @@ typedef struct klmc_params {
     int32_t boundary;      /* KLMC_PERIODIC                                      */
     int32_t packing;       /* device store: KLMC_PACK_BIT (1 bit/site), _BYTE, or
                               _AUTO (= BIT)                                       */
-    int32_t reserved0;
+    int32_t cluster;       /* CTAs that share one lattice in the resident sweep
+                              (a thread-block cluster, 1..16); 0 = automatic      */
     int64_t n_A;           /* number of A lipids; -1 = floor(fraction_A*N + 0.5)  */
     double fraction_A;     /* used when n_A < 0; in [0, 1]                        */
     double omega_over_kT;  /* omega_AB / kT, finite; E/kT = omega/kT * n_unlike   */
@@ -104,8 +105,9 @@ klmc_status klmc_create_ex(klmc_ctx **out, const klmc_params *p);
  * phases of exchange attempts, N attempts when 4 | Lx and 4 | Ly (section
  * "Massive Parallel Kawasaki Kinetics": one MPKK step = as many attempts as
  * sites).  Deterministic: the result depends only on seed, the lattice and the
- * absolute sweep index.  EINVAL when the lattice is too large for the
- * shared-memory resident path (padded bit rows must fit one CTA). */
+ * absolute sweep index, not on the cluster size.  EINVAL when the lattice is
+ * too large for the shared-memory resident path (each CTA's band of padded bit
+ * rows plus four halo rows must fit its shared memory). */
 klmc_status klmc_sweep(klmc_ctx *c, int64_t n_mcs);
 
 /* As klmc_sweep, and records n_unlike after every trace_every-th step into the
@@ -150,8 +152,19 @@ klmc_status klmc_get_lattice(klmc_ctx *c, uint8_t *host_out, int64_t n);
  * reproduces the uninterrupted run exactly. */
 klmc_status klmc_set_lattice(klmc_ctx *c, const uint8_t *host_in, int64_t n, int64_t sweep_index);
 
-/* Lattice sides, geometry and n_A of a handle.  Any pointer may be NULL. */
+/* As klmc_set_lattice from a caller device buffer (n = Lx*Ly bytes, each 0 or
+ * 1, not checked), enqueued without synchronising; n_A is recounted on the
+ * device and reported by klmc_get_shape. */
+klmc_status klmc_set_lattice_device(klmc_ctx *c, const uint8_t *dev_in, int64_t n,
+                                    int64_t sweep_index);
+
+/* Lattice sides, geometry and n_A of a handle.  Any pointer may be NULL.
+ * Synchronises when n_A was last set on the device. */
 klmc_status klmc_get_shape(klmc_ctx *c, int32_t *Lx, int32_t *Ly, int32_t *geometry, int64_t *n_A);
+
+/* Launch shape of the handle's resident sweep: CTAs per lattice (thread-block
+ * cluster size) and threads per CTA.  Either pointer may be NULL. */
+klmc_status klmc_get_launch(klmc_ctx *c, int32_t *cluster, int32_t *threads_per_cta);
 
 /* Waits for all work enqueued on the handle's stream. */
 klmc_status klmc_synchronize(klmc_ctx *c);
@@ -161,8 +174,9 @@ klmc_status klmc_synchronize(klmc_ctx *c);
 klmc_status klmc_destroy(klmc_ctx *c);
 
 /* Batched form: n independent replicas (own sizes, compositions, omega, seeds)
- * advanced together by one launch of the resident kernel, one CTA per replica.
- * All replicas use the stream of reps[0]. */
+ * advanced together by one launch of the resident kernel, one thread-block
+ * cluster per replica (the smallest cluster size any replica asks for).  All
+ * replicas use the stream of reps[0]. */
 klmc_status klmc_batch_create(klmc_batch **out, const klmc_params *reps, int32_t n);
 
 /* Enqueues n_mcs[i] steps for replica i (entries may differ; 0 skips). */

@@ -30,7 +30,7 @@ FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void
 class Params(ctypes.Structure):
     _fields_ = [("Lx", ctypes.c_int32), ("Ly", ctypes.c_int32), ("geometry", ctypes.c_int32),
                 ("boundary", ctypes.c_int32), ("packing", ctypes.c_int32),
-                ("reserved0", ctypes.c_int32), ("n_A", ctypes.c_int64),
+                ("cluster", ctypes.c_int32), ("n_A", ctypes.c_int64),
                 ("fraction_A", ctypes.c_double), ("omega_over_kT", ctypes.c_double),
                 ("seed", ctypes.c_uint64), ("alloc", ALLOC_FN), ("free", FREE_FN),
                 ("user", ctypes.c_void_p), ("stream", ctypes.c_void_p)]
@@ -86,7 +86,9 @@ def lib():
         "klmc_get_counters": [vp, P(Counters)],
         "klmc_get_lattice": [vp, vp, i64],
         "klmc_set_lattice": [vp, vp, i64, i64],
+        "klmc_set_lattice_device": [vp, vp, i64, i64],
         "klmc_get_shape": [vp, P(i32), P(i32), P(i32), P(i64)],
+        "klmc_get_launch": [vp, P(i32), P(i32)],
         "klmc_synchronize": [vp],
         "klmc_destroy": [vp],
         "klmc_batch_create": [P(vp), P(Params), i32],
@@ -144,7 +146,8 @@ class _TorchAllocator:
 
 def make_params(Lx: int, Ly: int | None = None, *, geometry: int = TRI6, packing: int = PACK_BIT,
                 n_A: int = -1, fraction_A: float = 0.5, omega_over_kT: float = 0.0, seed: int = 1,
-                stream: int | None = None, allocator: _TorchAllocator | None = None) -> Params:
+                cluster: int = 0, stream: int | None = None,
+                allocator: _TorchAllocator | None = None) -> Params:
     p = Params()
     _check(lib().klmc_params_default(ctypes.byref(p)))
     p.Lx = int(Lx)
@@ -155,6 +158,7 @@ def make_params(Lx: int, Ly: int | None = None, *, geometry: int = TRI6, packing
     p.fraction_A = float(fraction_A)
     p.omega_over_kT = float(omega_over_kT)
     p.seed = int(seed)
+    p.cluster = int(cluster)
     p.stream = stream
     if allocator is not None:
         p.alloc = allocator.alloc
@@ -167,7 +171,7 @@ class Lattice:
 
     def __init__(self, Lx: int, Ly: int | None = None, *, geometry: int = TRI6,
                  packing: int = PACK_BIT, n_A: int = -1, fraction_A: float = 0.5,
-                 omega_over_kT: float = 0.0, seed: int = 1, stream=None,
+                 omega_over_kT: float = 0.0, seed: int = 1, cluster: int = 0, stream=None,
                  torch_allocator: bool = True, _handle=None, _owner=None):
         import torch
 
@@ -180,7 +184,8 @@ class Lattice:
             self._alloc = _TorchAllocator(dev) if torch_allocator else None
             p = make_params(Lx, Ly, geometry=geometry, packing=packing, n_A=n_A,
                             fraction_A=fraction_A, omega_over_kT=omega_over_kT, seed=seed,
-                            stream=_torch_stream_handle(stream), allocator=self._alloc)
+                            cluster=cluster, stream=_torch_stream_handle(stream),
+                            allocator=self._alloc)
             h = ctypes.c_void_p()
             _check(lib().klmc_create_ex(ctypes.byref(h), ctypes.byref(p)))
             self._h = h
@@ -254,6 +259,17 @@ class Lattice:
     def set_lattice(self, t, sweep_index: int = 0):
         arr = np.ascontiguousarray(np.asarray(t, dtype=np.uint8).ravel())
         _check(lib().klmc_set_lattice(self._h, arr.ctypes.data, arr.size, int(sweep_index)))
+
+    def set_lattice_device(self, t, sweep_index: int = 0):
+        """Loads the lattice from a uint8 CUDA tensor of Lx*Ly entries (0/1), async."""
+        assert t.is_cuda and t.dtype.itemsize == 1 and t.numel() == self.N and t.is_contiguous()
+        _check(lib().klmc_set_lattice_device(self._h, t.data_ptr(), self.N, int(sweep_index)))
+
+    def launch_shape(self):
+        """(CTAs per lattice, threads per CTA) of the resident sweep."""
+        c, t = ctypes.c_int32(), ctypes.c_int32()
+        _check(lib().klmc_get_launch(self._h, ctypes.byref(c), ctypes.byref(t)))
+        return c.value, t.value
 
     def synchronize(self):
         _check(lib().klmc_synchronize(self._h))

@@ -58,7 +58,9 @@ bool device_ok(std::string *why)
 struct klmc_ctx {
     klmc_params p;
     long long N = 0, nA = 0;
+    bool nA_on_device = false;    // nA must be read back from state[kNA]
     int W = 0, pitch = 0;
+    int cluster = 1;              // CTAs per lattice in the resident sweep
     size_t lat_bytes = 0;
     void *lat = nullptr;
     long long *state = nullptr;   // StateSlot array
@@ -125,7 +127,22 @@ klmc_status validate(const klmc_params *p)
         return fail(KLMC_EINVAL, "fraction_A must be in [0, 1]");
     if (p->n_A > N) return fail(KLMC_EINVAL, "n_A must be in [0, Lx*Ly]");
     if (p->alloc && !p->free) return fail(KLMC_EINVAL, "alloc given without free");
+    if (p->cluster < 0 || p->cluster > 16) return fail(KLMC_EINVAL, "cluster must be in [0, 16]");
+    if (p->cluster > 1 && p->Ly / p->cluster < 4)
+        return fail(KLMC_EINVAL, "cluster too large: every band needs >= 4 rows");
     return KLMC_OK;
+}
+
+// Automatic cluster size: the smallest power of two whose bands fit in shared
+// memory, raised while every band keeps >= 24 rows (more CTAs shorten each phase;
+// too-thin bands spend their time on halos and barriers).
+int auto_cluster(int Lx, int Ly)
+{
+    const int cmax = resident_max_cluster(Ly);
+    int c = 1;
+    while (c < cmax && resident_smem_bytes(Lx, Ly, c) > (size_t)resident_max_smem_bytes()) c *= 2;
+    while (c * 2 <= cmax && Ly / (c * 2) >= 24) c *= 2;
+    return c;
 }
 
 // Acceptance table (Metropolis step c with u = r / 2^32): a pair whose
@@ -198,6 +215,7 @@ klmc_status create_one(klmc_ctx **out, const klmc_params *p, klmc_batch *owner)
     c->N = (long long)p->Lx * p->Ly;
     c->nA = p->n_A >= 0 ? p->n_A : (long long)floor(p->fraction_A * (double)c->N + 0.5);
     c->W = (p->Lx + 31) / 32;
+    c->cluster = p->cluster > 0 ? p->cluster : auto_cluster(p->Lx, p->Ly);
     if (c->p.packing == KLMC_PACK_BIT) {
         c->pitch = (c->W + 3) / 4 * 4;  // 16-byte rows
         c->lat_bytes = (size_t)c->pitch * 4 * p->Ly;
@@ -250,12 +268,13 @@ klmc_status create_one(klmc_ctx **out, const klmc_params *p, klmc_batch *owner)
     return KLMC_OK;
 }
 
-klmc_status check_resident(const klmc_ctx *c)
+klmc_status check_resident(const klmc_ctx *c, int cluster)
 {
-    if (resident_smem_bytes(c->p.Lx, c->p.Ly) > (size_t)resident_max_smem_bytes())
+    const size_t need = resident_smem_bytes(c->p.Lx, c->p.Ly, cluster);
+    if (need > (size_t)resident_max_smem_bytes())
         return fail(KLMC_EINVAL, "lattice too large for the shared-memory resident sweep (" +
-                                     std::to_string(resident_smem_bytes(c->p.Lx, c->p.Ly)) +
-                                     " bytes of padded bit rows)");
+                                     std::to_string(need) + " bytes of padded bit rows per CTA at " +
+                                     std::to_string(cluster) + " CTAs per lattice)");
     return KLMC_OK;
 }
 
@@ -266,14 +285,18 @@ klmc_status sweep_one(klmc_ctx *c, int64_t n_mcs, int64_t trace_every, int64_t *
     if (trace_every < 0 || (trace_every > 0 && !dev_trace))
         return fail(KLMC_EINVAL, "trace_every > 0 needs a device trace buffer");
     if (n_mcs == 0) return KLMC_OK;
-    klmc_status st = check_resident(c);
+    klmc_status st = check_resident(c, c->cluster);
     if (st != KLMC_OK) return st;
+    if (trace_every > 0 && n_mcs / trace_every > 0)
+        KLMC_CUDA(cudaMemsetAsync(dev_trace, 0, (size_t)(n_mcs / trace_every) * sizeof(int64_t),
+                                  c->stream));
     SweepCall call;
     call.sweep0 = c->sweep;
     call.n_mcs = n_mcs;
     call.trace = (long long *)dev_trace;
     call.trace_every = trace_every;
-    KLMC_CUDA(launch_resident_sweep_one(c->job, call, resident_smem_bytes(c->p.Lx, c->p.Ly),
+    KLMC_CUDA(launch_resident_sweep_one(c->job, call, c->cluster,
+                                        resident_smem_bytes(c->p.Lx, c->p.Ly, c->cluster),
                                         c->stream));
     c->sweep += n_mcs;
     return KLMC_OK;
@@ -440,6 +463,24 @@ klmc_status klmc_set_lattice(klmc_ctx *c, const uint8_t *host_in, int64_t n, int
     KLMC_CUDA(cudaMemcpyAsync(&nA, c->state + kScratch0, sizeof(nA), cudaMemcpyDeviceToHost, c->stream));
     KLMC_CUDA(cudaStreamSynchronize(c->stream));
     c->nA = nA;
+    c->nA_on_device = false;
+    c->sweep = sweep_index;
+    return KLMC_OK;
+}
+
+klmc_status klmc_set_lattice_device(klmc_ctx *c, const uint8_t *dev_in, int64_t n,
+                                    int64_t sweep_index)
+{
+    if (!c || !dev_in) return fail(KLMC_EINVAL, "NULL argument");
+    if (n != c->N) return fail(KLMC_EINVAL, "n must equal Lx*Ly");
+    if (sweep_index < 0) return fail(KLMC_EINVAL, "sweep_index must be >= 0");
+    KLMC_CUDA(launch_pack(dev_in, c->lat, c->job.packing, c->p.Lx, c->p.Ly, c->pitch, c->stream));
+    KLMC_CUDA(cudaMemsetAsync(c->state, 0, kStateSlots * sizeof(long long), c->stream));
+    KLMC_CUDA(launch_recount(c->lat, c->job.packing, c->p.Lx, c->p.Ly, c->pitch, c->p.geometry,
+                             c->state + kNUnlike, c->stream));
+    KLMC_CUDA(launch_count_A(c->lat, c->job.packing, c->p.Lx, c->p.Ly, c->pitch, c->state + kNA,
+                             c->stream));
+    c->nA_on_device = true;
     c->sweep = sweep_index;
     return KLMC_OK;
 }
@@ -447,10 +488,25 @@ klmc_status klmc_set_lattice(klmc_ctx *c, const uint8_t *host_in, int64_t n, int
 klmc_status klmc_get_shape(klmc_ctx *c, int32_t *Lx, int32_t *Ly, int32_t *geometry, int64_t *n_A)
 {
     if (!c) return fail(KLMC_EINVAL, "ctx is NULL");
+    if (n_A && c->nA_on_device) {
+        long long v = 0;
+        KLMC_CUDA(cudaMemcpyAsync(&v, c->state + kNA, sizeof(v), cudaMemcpyDeviceToHost, c->stream));
+        KLMC_CUDA(cudaStreamSynchronize(c->stream));
+        c->nA = v;
+        c->nA_on_device = false;
+    }
     if (Lx) *Lx = c->p.Lx;
     if (Ly) *Ly = c->p.Ly;
     if (geometry) *geometry = c->p.geometry;
     if (n_A) *n_A = c->nA;
+    return KLMC_OK;
+}
+
+klmc_status klmc_get_launch(klmc_ctx *c, int32_t *cluster, int32_t *threads_per_cta)
+{
+    if (!c) return fail(KLMC_EINVAL, "ctx is NULL");
+    if (cluster) *cluster = c->cluster;
+    if (threads_per_cta) *threads_per_cta = resident_threads(c->cluster);
     return KLMC_OK;
 }
 
@@ -481,7 +537,7 @@ klmc_status klmc_batch_create(klmc_batch **out, const klmc_params *reps, int32_t
         p.stream = reps[0].stream;
         klmc_ctx *c = nullptr;
         klmc_status st = create_one(&c, &p, b);
-        if (st == KLMC_OK) st = check_resident(c);
+        if (st == KLMC_OK) st = check_resident(c, c->cluster);
         if (st != KLMC_OK) {
             std::string msg = "replica " + std::to_string(i) + ": " + g_err;
             if (c) {
@@ -519,7 +575,7 @@ klmc_status klmc_batch_sweep(klmc_batch *b, const int64_t *n_mcs)
 {
     if (!b || !n_mcs) return fail(KLMC_EINVAL, "NULL argument");
     const int n = (int)b->reps.size();
-    size_t smem = 0;
+    int cluster = 16;
     bool any = false;
     for (int i = 0; i < n; ++i) {
         if (n_mcs[i] < 0) return fail(KLMC_EINVAL, "n_mcs entries must be >= 0");
@@ -531,14 +587,22 @@ klmc_status klmc_batch_sweep(klmc_batch *b, const int64_t *n_mcs)
         call.trace_every = 0;
         if (n_mcs[i] > 0) {
             any = true;
-            const size_t s = resident_smem_bytes(c->p.Lx, c->p.Ly);
-            if (s > smem) smem = s;
+            if (c->cluster < cluster) cluster = c->cluster;
         }
     }
     if (!any) return KLMC_OK;
+    size_t smem = 0;
+    for (int i = 0; i < n; ++i) {
+        if (n_mcs[i] == 0) continue;
+        klmc_ctx *c = b->reps[i];
+        klmc_status st = check_resident(c, cluster);
+        if (st != KLMC_OK) return st;
+        const size_t s = resident_smem_bytes(c->p.Lx, c->p.Ly, cluster);
+        if (s > smem) smem = s;
+    }
     KLMC_CUDA(cudaMemcpyAsync(b->dcalls, b->hcalls.data(), sizeof(SweepCall) * (size_t)n,
                               cudaMemcpyHostToDevice, b->stream));
-    KLMC_CUDA(launch_resident_sweep(b->djobs, b->dcalls, n, smem, b->stream));
+    KLMC_CUDA(launch_resident_sweep(b->djobs, b->dcalls, n, cluster, smem, b->stream));
     for (int i = 0; i < n; ++i) b->reps[i]->sweep += n_mcs[i];
     return KLMC_OK;
 }

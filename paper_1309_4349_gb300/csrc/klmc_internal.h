@@ -20,6 +20,7 @@ enum StateSlot : int {
     kDraws = 3,
     kAccepts = 4,
     kScratch0 = 5,  // recount result
+    kNA = 6,        // A-site count after a device-side lattice load
     kStateSlots = 8
 };
 
@@ -48,16 +49,20 @@ struct SweepCall {
     long long trace_every;
 };
 
-// Shared memory needed by the resident kernel for a job (bytes).
-size_t resident_smem_bytes(int Lx, int Ly);
+// Dynamic shared memory per CTA for a lattice split over `cluster` CTAs (bytes),
+// the per-CTA limit, and the largest cluster whose bands keep >= 4 rows.
+size_t resident_smem_bytes(int Lx, int Ly, int cluster);
 int resident_max_smem_bytes();
+int resident_max_cluster(int Ly);
+int resident_threads(int cluster);
 
-// Batched launch: one CTA per job, job/call tables in device memory.
+// Batched launch: one cluster of `cluster` CTAs per job, tables in device memory.
+// The trace buffers of the calls must be zeroed before the launch.
 cudaError_t launch_resident_sweep(const SweepJob *d_jobs, const SweepCall *d_calls, int n_jobs,
-                                  size_t smem_bytes, cudaStream_t stream);
+                                  int cluster, size_t smem_bytes, cudaStream_t stream);
 // Single lattice: job and call passed by value as kernel parameters.
-cudaError_t launch_resident_sweep_one(const SweepJob &job, const SweepCall &call, size_t smem_bytes,
-                                      cudaStream_t stream);
+cudaError_t launch_resident_sweep_one(const SweepJob &job, const SweepCall &call, int cluster,
+                                      size_t smem_bytes, cudaStream_t stream);
 
 // Initial placement: the nA sites with the smallest (64-bit Philox key, index).
 cudaError_t launch_init_lattice(void *lat, int packing, int Lx, int Ly, int pitch, uint32_t key0,

@@ -1,21 +1,31 @@
-// sweep_resident.cu -- Kawasaki exchange sweeps with the whole lattice resident in
-// shared memory, one CTA per lattice (section "Massive Parallel Kawasaki Kinetics":
-// every iteration performs one exchange per domain of a random decomposition, all
-// in parallel; here the decomposition is a conflict-free shifted sublattice phase).
+// sweep_resident.cu -- Kawasaki exchange sweeps with the lattice resident in shared
+// memory for the whole launch (section "Massive Parallel Kawasaki Kinetics": every
+// iteration performs one exchange per domain of a random decomposition, all in
+// parallel; here the decomposition is a conflict-free shifted sublattice phase).
 //
-// Shared-memory layout: row y is RW 32-bit words holding the padded bit positions
-// pos in [-32, 32*RW - 32); position pos holds site (pos mod Lx, y).  Every copy of
-// a site is kept equal, so the 32-site window starting at any x in [-32, Lx + 32]
+// Work split.  One lattice per thread-block cluster of C CTAs (C = 1 is a plain
+// CTA).  CTA c of the cluster owns the row band [Y_c, Y_c+1), Y_c = floor(c Ly / C),
+// and keeps band rows plus two halo rows on each side in shared memory: local row
+// lr holds global row (Y_c - 2 + lr) mod Ly.  A phase's anchor rows are split by
+// band; every read of an anchor's neighbourhood (rows y-2 .. y+2) is local.  An
+// accepted exchange flips its two sites in every copy of their rows: the local
+// copy and, for rows within two of a band edge, the copies held by the
+// neighbouring CTAs, through distributed shared memory.  Phases are separated by
+// a cluster barrier (release/acquire), so the next phase sees every flip.
+//
+// Row layout.  A shared-memory row is RW 32-bit words holding the padded bit
+// positions pos in [-32, 32*RW - 32); position pos holds site (pos mod Lx).  All
+// copies are kept equal, so the 32-site window starting at any x in [-32, Lx + 32]
 // is one funnel shift of two words.
 //
-// One thread handles the anchors of one 32-site word of one anchor row.  The
-// neighbour comparisons of all 32 positions are formed with bitwise operations
-// and summed with a carry-save adder tree into bit planes of S = same_a + same_b,
-// the number of neighbours of a (other than b) equal to a plus those of b (other
-// than a) equal to b.  An exchange changes the unlike-contact count by
-// dn = 2 (S - (z - 1)).  Only positions whose S lies in the draw range draw a
-// Philox number; the rest of the unlike pairs are accepted outright (Metropolis
-// acceptance min{1, exp(-omega dn / kT)}, Metropolis steps a-c).
+// Evaluation.  One thread handles the anchors of one 32-site word of one anchor
+// row.  Neighbour comparisons of all 32 positions are bitwise operations summed by
+// a carry-save adder tree into bit planes of S = same_a + same_b (neighbours of a,
+// other than b, equal to a, plus neighbours of b, other than a, equal to b).  An
+// exchange changes the number of unlike contacts by dn = 2 (S - (z - 1)).  Unlike
+// pairs whose S lies in the draw range draw a Philox number; the rest are accepted
+// outright (Metropolis acceptance min{1, exp(-omega dn / kT)}, steps a-c).  The
+// draws of a warp are spread evenly over its 32 lanes before Philox runs.
 #include <string.h>
 
 #include "klmc_internal.h"
@@ -23,11 +33,10 @@
 namespace klmc {
 namespace {
 
-constexpr int kThreads = 1024;
-constexpr int kWarps = kThreads / 32;
-
 struct PhaseP {
-    int oi, rx, ry, px, py, Kx, My, ntask, umax;
+    int oi, rx, ry, px, py, umax;
+    int a1, n1, a2, n2, M1;  // this band's anchor rows: m in [a1, a1+n1) u [a2, a2+n2)
+    int ntask;
 };
 
 // Philox4x32-10 (Salmon et al., SC'11): ten rounds of two 32x32->64 products,
@@ -57,28 +66,42 @@ __device__ __forceinline__ Philox4 philox4(uint32_t c0, uint32_t c1, uint32_t c2
     return out;
 }
 
-// Phase parameters of (sweep s, phase f): orientation index, shift, sublattice
-// periods and counts.  Orientation 1 is (0,1) in both geometries.
-__device__ void phase_params(int geometry, int Lx, int Ly, int W, uint32_t k0, uint32_t k1,
-                             long long s, int f, PhaseP *P)
+__device__ __forceinline__ int floor_div(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
+__device__ __forceinline__ int ceil_div(int a, int b) { return -floor_div(-a, b); }
+
+// Phase parameters of (sweep s, phase f) and this band's share of its anchor rows.
+// Orientation 1 is (0,1) in both geometries.
+__device__ void phase_params(int geometry, int Lx, int Ly, int W, int Y0, int Y1, uint32_t k0,
+                             uint32_t k1, long long s, int f, PhaseP *P)
 {
     Philox4 w = philox4(0xFFFFFFFFu, (uint32_t)f, (uint32_t)(unsigned long long)s,
                         (uint32_t)((unsigned long long)s >> 32), k0, k1);
-    int nO = geometry == kTRI6 ? 3 : 2;
-    P->oi = (int)__umulhi(w.v[0], (uint32_t)nO);
-    P->rx = (int)__umulhi(w.v[1], (uint32_t)Lx);
-    P->ry = (int)__umulhi(w.v[2], (uint32_t)Ly);
-    if (P->oi == 1) {
-        P->px = 2; P->py = 4;
-        P->Kx = (Lx - 2) / 2 + 1;
-        P->My = (Ly - 3) / 4 + 1;
+    const int nO = geometry == kTRI6 ? 3 : 2;
+    const int oi = (int)__umulhi(w.v[0], (uint32_t)nO);
+    const int rx = (int)__umulhi(w.v[1], (uint32_t)Lx);
+    const int ry = (int)__umulhi(w.v[2], (uint32_t)Ly);
+    int px, py, Kx, My;
+    if (oi == 1) {
+        px = 2; py = 4;
+        Kx = (Lx - 2) / 2 + 1;
+        My = (Ly - 3) / 4 + 1;
     } else {
-        P->px = 4; P->py = 2;
-        P->Kx = (Lx - 3) / 4 + 1;
-        P->My = (Ly - 2) / 2 + 1;
+        px = 4; py = 2;
+        Kx = (Lx - 3) / 4 + 1;
+        My = (Ly - 2) / 2 + 1;
     }
-    P->ntask = P->My * W;
-    P->umax = P->px * (P->Kx - 1);
+    // Anchor rows y_m = (ry + py m) mod Ly, m < My: unwrapped for m < M1.
+    const int M1 = min(My, ceil_div(Ly - ry, py));
+    const int a1 = max(ceil_div(Y0 - ry, py), 0);
+    const int b1 = min(floor_div(Y1 - 1 - ry, py), M1 - 1);
+    const int a2 = max(ceil_div(Y0 + Ly - ry, py), M1);
+    const int b2 = min(floor_div(Y1 - 1 + Ly - ry, py), My - 1);
+    P->oi = oi; P->rx = rx; P->ry = ry; P->px = px; P->py = py;
+    P->umax = px * (Kx - 1);
+    P->a1 = a1; P->n1 = max(0, b1 - a1 + 1);
+    P->a2 = a2; P->n2 = max(0, b2 - a2 + 1);
+    P->M1 = M1;
+    P->ntask = (P->n1 + P->n2) * W;
 }
 
 // Bits p of the word at x0 with x0 + p in [lo, hi].
@@ -175,8 +198,27 @@ __device__ __forceinline__ uint32_t ge_const(const Planes &S, int c)
 
 __device__ __forceinline__ uint32_t eqm(uint32_t v, uint32_t t) { return ~(v ^ t); }
 
-// XOR mask into padded buffer bit positions q .. q+31 of one row (clipped).
-__device__ __forceinline__ void xor_at(uint32_t *row, int RW, int q, uint32_t mask)
+__device__ __forceinline__ uint32_t smem_addr(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// XOR v into the 32-bit word at shared address addr of CTA `rank` of the cluster.
+__device__ __forceinline__ void xor_word(uint32_t addr, uint32_t rank, bool local, uint32_t v)
+{
+    if (v == 0u) return;
+    if (local) {
+        asm volatile("red.shared.xor.b32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+    } else {
+        uint32_t remote;
+        asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(addr), "r"(rank));
+        asm volatile("red.shared::cluster.xor.b32 [%0], %1;" ::"r"(remote), "r"(v) : "memory");
+    }
+}
+
+// XOR mask into padded bit positions q .. q+31 of the row at shared address row (clipped).
+__device__ __forceinline__ void xor_at(uint32_t row, int RW, int q, uint32_t mask, uint32_t rank,
+                                       bool local)
 {
     if (q < 0) {
         if (q <= -32) return;
@@ -184,16 +226,17 @@ __device__ __forceinline__ void xor_at(uint32_t *row, int RW, int q, uint32_t ma
         q = 0;
     }
     const int w = q >> 5, s = q & 31;
-    if (w < RW) atomicXor(row + w, mask << s);
-    if (s != 0 && w + 1 < RW) atomicXor(row + w + 1, mask >> (32 - s));
+    if (w < RW) xor_word(row + 4u * w, rank, local, mask << s);
+    if (s != 0 && w + 1 < RW) xor_word(row + 4u * (w + 1), rank, local, mask >> (32 - s));
 }
 
-// Flip the sites at positions pos + p (mask bit p) and every padded copy.
-__device__ __forceinline__ void flip_sites(uint32_t *row, int RW, int Lx, int pos, uint32_t mask)
+// Flip the sites at positions pos + p (mask bit p) in one row copy, every padded copy.
+__device__ __forceinline__ void flip_row(uint32_t row, int RW, int Lx, int pos, uint32_t mask,
+                                         uint32_t rank, bool local)
 {
     const int q = pos + 32;
-    for (int qq = q; qq > -32; qq -= Lx) xor_at(row, RW, qq, mask);
-    for (int qq = q + Lx; qq < 32 * RW; qq += Lx) xor_at(row, RW, qq, mask);
+    for (int qq = q; qq > -32; qq -= Lx) xor_at(row, RW, qq, mask, rank, local);
+    for (int qq = q + Lx; qq < 32 * RW; qq += Lx) xor_at(row, RW, qq, mask, rank, local);
 }
 
 struct Geo {
@@ -202,6 +245,8 @@ struct Geo {
     uint32_t k0, k1;
     int draw_lo, draw_hi;
     int zm1;
+    int C, rank, Y0, Y1;
+    uint32_t lat_addr;  // shared address of local row 0
 };
 
 struct Acc {
@@ -209,121 +254,187 @@ struct Acc {
     int32_t dn;
 };
 
-__device__ __forceinline__ const uint32_t *row_ptr(const uint32_t *lat, const Geo &g, int y)
+// Flip global row r (unwrapped, in [Y0 - 1, Y1]) in every CTA that holds a copy.
+__device__ __forceinline__ void flip_global_row(const Geo &g, int r, int pos, uint32_t mask)
 {
-    if (y < 0) y += g.Ly;
-    if (y >= g.Ly) y -= g.Ly;
-    return lat + (size_t)y * g.RW;
+    const int lr_self = r - g.Y0 + 2;
+    if (g.C == 1) {
+        // Rows 0, 1 and Ly-2, Ly-1 also live in the opposite halo.
+        const int gr = r < 0 ? r + g.Ly : (r >= g.Ly ? r - g.Ly : r);
+        for (int lr = gr + 2 >= g.Ly ? gr + 2 - g.Ly : gr + 2; lr < g.Ly + 4; lr += g.Ly)
+            flip_row(g.lat_addr + 4u * (uint32_t)(lr * g.RW), g.RW, g.Lx, pos, mask, 0u, true);
+        return;
+    }
+    if (lr_self >= 4 && lr_self < g.Y1 - g.Y0) {  // interior row: only the local copy
+        flip_row(g.lat_addr + 4u * (uint32_t)(lr_self * g.RW), g.RW, g.Lx, pos, mask, 0u, true);
+        return;
+    }
+    const int gr = r < 0 ? r + g.Ly : (r >= g.Ly ? r - g.Ly : r);
+    const int cand[3] = {g.rank == 0 ? g.C - 1 : g.rank - 1, g.rank,
+                         g.rank + 1 == g.C ? 0 : g.rank + 1};
+    for (int k = 0; k < 3; ++k) {
+        const int d = cand[k];
+        if (k == 2 && d == cand[0]) break;  // C == 2: both neighbours are the same CTA
+        const int Yd = (int)(((long long)d * g.Ly) / g.C);
+        const int Hd = (int)(((long long)(d + 1) * g.Ly) / g.C) - Yd;
+        int lr = gr - Yd + 2;
+        lr %= g.Ly;
+        if (lr < 0) lr += g.Ly;
+        for (; lr < Hd + 4; lr += g.Ly)
+            flip_row(g.lat_addr + 4u * (uint32_t)(lr * g.RW), g.RW, g.Lx, pos, mask, (uint32_t)d,
+                     d == g.rank);
+    }
 }
 
-// One phase of one lattice: every task is (anchor row m, word j).
-template <int G, int OI>
-__device__ __forceinline__ void run_phase(uint32_t *lat, const Geo &g, const PhaseP &P,
-                                          const uint64_t *thr, int f, uint32_t s_lo,
-                                          uint32_t s_hi, Acc &A)
+__device__ __forceinline__ void phase_barrier(int C)
+{
+    if (C == 1) {
+        __syncthreads();
+    } else {
+        asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory");
+        asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+    }
+}
+
+// One phase of one band.  Every task is (anchor row, word j).  The task loop runs
+// in whole warps so that a warp's draws can be redistributed over its lanes.
+template <int G, int OI, int THREADS>
+__device__ __forceinline__ void run_phase(const uint32_t *lat, const Geo &g, const PhaseP &P,
+                                          const uint64_t *thr, uint32_t *warp_acc, int f,
+                                          uint32_t s_lo, uint32_t s_hi, Acc &A)
 {
     // b = a + o: (1,0) -> same row, +1; (0,1) -> next row; (1,-1) -> previous row, +1
     constexpr int bdy = OI == 0 ? 0 : (OI == 1 ? 1 : -1);
     constexpr int bdx = OI == 1 ? 0 : 1;
-    for (int t = threadIdx.x; t < P.ntask; t += kThreads) {
-        const int m = (int)(((unsigned long long)t * g.magicW) >> 32);
-        const int j = t - m * g.W;
-        int y = P.ry + P.py * m;
-        if (y >= g.Ly) y -= g.Ly;
-        const int x0 = j << 5;
-        const uint32_t am = anchor_mask(x0, P, g.Lx);
-        if (am == 0u) continue;
-
-        uint32_t ta, tb;
-        Planes S;
-        const uint32_t *r0 = row_ptr(lat, g, y);
-        const uint32_t a0 = r0[j], a1 = r0[j + 1], a2 = r0[j + 2];
-        const uint32_t Am = fsr(a0, a1, 31), A0 = a1, A1 = fsr(a1, a2, 1);
-        if (G == kTRI6 && OI == 0) {
-            const uint32_t *rm = row_ptr(lat, g, y - 1), *rp = row_ptr(lat, g, y + 1);
-            const uint32_t m1 = rm[j + 1], m2 = rm[j + 2];
-            const uint32_t p0 = rp[j], p1 = rp[j + 1], p2 = rp[j + 2];
-            const uint32_t M0 = m1, M1 = fsr(m1, m2, 1), M2 = fsr(m1, m2, 2);
-            const uint32_t A2 = fsr(a1, a2, 2);
-            const uint32_t Pm = fsr(p0, p1, 31), P0 = p1, P1 = fsr(p1, p2, 1);
-            ta = A0; tb = A1;
-            S = count10(eqm(Am, ta), eqm(P0, ta), eqm(M0, ta), eqm(M1, ta), eqm(Pm, ta),
-                        eqm(A2, tb), eqm(P1, tb), eqm(M1, tb), eqm(M2, tb), eqm(P0, tb));
-        } else if (G == kTRI6 && OI == 1) {
-            const uint32_t *rm = row_ptr(lat, g, y - 1), *rp = row_ptr(lat, g, y + 1),
-                           *rq = row_ptr(lat, g, y + 2);
-            const uint32_t m1 = rm[j + 1], m2 = rm[j + 2];
-            const uint32_t p0 = rp[j], p1 = rp[j + 1], p2 = rp[j + 2];
-            const uint32_t q0 = rq[j], q1 = rq[j + 1];
-            const uint32_t M0 = m1, M1 = fsr(m1, m2, 1);
-            const uint32_t Pm = fsr(p0, p1, 31), P0 = p1, P1 = fsr(p1, p2, 1);
-            const uint32_t Qm = fsr(q0, q1, 31), Q0 = q1;
-            ta = A0; tb = P0;
-            S = count10(eqm(A1, ta), eqm(Am, ta), eqm(M0, ta), eqm(M1, ta), eqm(Pm, ta),
-                        eqm(P1, tb), eqm(Pm, tb), eqm(Q0, tb), eqm(A1, tb), eqm(Qm, tb));
-        } else if (G == kTRI6 && OI == 2) {
-            const uint32_t *rn = row_ptr(lat, g, y - 2), *rm = row_ptr(lat, g, y - 1),
-                           *rp = row_ptr(lat, g, y + 1);
-            const uint32_t n1 = rn[j + 1], n2 = rn[j + 2];
-            const uint32_t m1 = rm[j + 1], m2 = rm[j + 2];
-            const uint32_t p0 = rp[j], p1 = rp[j + 1];
-            const uint32_t N1 = fsr(n1, n2, 1), N2 = fsr(n1, n2, 2);
-            const uint32_t M0 = m1, M1 = fsr(m1, m2, 1), M2 = fsr(m1, m2, 2);
-            const uint32_t Pm = fsr(p0, p1, 31), P0 = p1;
-            ta = A0; tb = M1;
-            S = count10(eqm(A1, ta), eqm(Am, ta), eqm(P0, ta), eqm(M0, ta), eqm(Pm, ta),
-                        eqm(M2, tb), eqm(M0, tb), eqm(A1, tb), eqm(N1, tb), eqm(N2, tb));
-        } else if (G == kSQ4 && OI == 0) {
-            const uint32_t *rm = row_ptr(lat, g, y - 1), *rp = row_ptr(lat, g, y + 1);
-            const uint32_t m1 = rm[j + 1], m2 = rm[j + 2];
-            const uint32_t p1 = rp[j + 1], p2 = rp[j + 2];
-            const uint32_t M0 = m1, M1 = fsr(m1, m2, 1);
-            const uint32_t A2 = fsr(a1, a2, 2);
-            const uint32_t P0 = p1, P1 = fsr(p1, p2, 1);
-            ta = A0; tb = A1;
-            S = count6(eqm(Am, ta), eqm(P0, ta), eqm(M0, ta), eqm(A2, tb), eqm(P1, tb),
-                       eqm(M1, tb));
-        } else {  // SQ4, (0,1)
-            const uint32_t *rm = row_ptr(lat, g, y - 1), *rp = row_ptr(lat, g, y + 1),
-                           *rq = row_ptr(lat, g, y + 2);
-            const uint32_t m1 = rm[j + 1];
-            const uint32_t p0 = rp[j], p1 = rp[j + 1], p2 = rp[j + 2];
-            const uint32_t q1 = rq[j + 1];
-            const uint32_t M0 = m1;
-            const uint32_t Pm = fsr(p0, p1, 31), P0 = p1, P1 = fsr(p1, p2, 1);
-            const uint32_t Q0 = q1;
-            ta = A0; tb = P0;
-            S = count6(eqm(A1, ta), eqm(Am, ta), eqm(M0, ta), eqm(P1, tb), eqm(Pm, tb),
-                       eqm(Q0, tb));
+    const int lane = threadIdx.x & 31;
+    for (int t0 = threadIdx.x & ~31; t0 < P.ntask; t0 += THREADS) {
+        const int t = t0 + lane;
+        uint32_t am = 0u, ta = 0u, tb = 0u;
+        Planes S = {0u, 0u, 0u, 0u};
+        int y = 0, x0 = 0;
+        if (t < P.ntask) {
+            const int mi = (int)(((unsigned long long)t * g.magicW) >> 32);
+            const int j = t - mi * g.W;
+            const int m = mi < P.n1 ? P.a1 + mi : P.a2 + (mi - P.n1);
+            y = P.ry + P.py * m;
+            if (y >= g.Ly) y -= g.Ly;
+            x0 = j << 5;
+            am = anchor_mask(x0, P, g.Lx);
+            const uint32_t *r0 = lat + (size_t)(y - g.Y0 + 2) * g.RW;
+            const uint32_t *rm = r0 - g.RW, *rp = r0 + g.RW;
+            const uint32_t a0 = r0[j], a1 = r0[j + 1], a2 = r0[j + 2];
+            const uint32_t Am = fsr(a0, a1, 31), A0 = a1, A1 = fsr(a1, a2, 1);
+            if (G == kTRI6 && OI == 0) {
+                const uint32_t m1 = rm[j + 1], m2 = rm[j + 2];
+                const uint32_t p0 = rp[j], p1 = rp[j + 1], p2 = rp[j + 2];
+                const uint32_t M0 = m1, M1 = fsr(m1, m2, 1), M2 = fsr(m1, m2, 2);
+                const uint32_t A2 = fsr(a1, a2, 2);
+                const uint32_t Pm = fsr(p0, p1, 31), P0 = p1, P1 = fsr(p1, p2, 1);
+                ta = A0; tb = A1;
+                S = count10(eqm(Am, ta), eqm(P0, ta), eqm(M0, ta), eqm(M1, ta), eqm(Pm, ta),
+                            eqm(A2, tb), eqm(P1, tb), eqm(M1, tb), eqm(M2, tb), eqm(P0, tb));
+            } else if (G == kTRI6 && OI == 1) {
+                const uint32_t *rq = rp + g.RW;
+                const uint32_t m1 = rm[j + 1], m2 = rm[j + 2];
+                const uint32_t p0 = rp[j], p1 = rp[j + 1], p2 = rp[j + 2];
+                const uint32_t q0 = rq[j], q1 = rq[j + 1];
+                const uint32_t M0 = m1, M1 = fsr(m1, m2, 1);
+                const uint32_t Pm = fsr(p0, p1, 31), P0 = p1, P1 = fsr(p1, p2, 1);
+                const uint32_t Qm = fsr(q0, q1, 31), Q0 = q1;
+                ta = A0; tb = P0;
+                S = count10(eqm(A1, ta), eqm(Am, ta), eqm(M0, ta), eqm(M1, ta), eqm(Pm, ta),
+                            eqm(P1, tb), eqm(Pm, tb), eqm(Q0, tb), eqm(A1, tb), eqm(Qm, tb));
+            } else if (G == kTRI6 && OI == 2) {
+                const uint32_t *rn = rm - g.RW;
+                const uint32_t n1 = rn[j + 1], n2 = rn[j + 2];
+                const uint32_t m1 = rm[j + 1], m2 = rm[j + 2];
+                const uint32_t p0 = rp[j], p1 = rp[j + 1];
+                const uint32_t N1 = fsr(n1, n2, 1), N2 = fsr(n1, n2, 2);
+                const uint32_t M0 = m1, M1 = fsr(m1, m2, 1), M2 = fsr(m1, m2, 2);
+                const uint32_t Pm = fsr(p0, p1, 31), P0 = p1;
+                ta = A0; tb = M1;
+                S = count10(eqm(A1, ta), eqm(Am, ta), eqm(P0, ta), eqm(M0, ta), eqm(Pm, ta),
+                            eqm(M2, tb), eqm(M0, tb), eqm(A1, tb), eqm(N1, tb), eqm(N2, tb));
+            } else if (G == kSQ4 && OI == 0) {
+                const uint32_t m1 = rm[j + 1], m2 = rm[j + 2];
+                const uint32_t p1 = rp[j + 1], p2 = rp[j + 2];
+                const uint32_t M0 = m1, M1 = fsr(m1, m2, 1);
+                const uint32_t A2 = fsr(a1, a2, 2);
+                const uint32_t P0 = p1, P1 = fsr(p1, p2, 1);
+                ta = A0; tb = A1;
+                S = count6(eqm(Am, ta), eqm(P0, ta), eqm(M0, ta), eqm(A2, tb), eqm(P1, tb),
+                           eqm(M1, tb));
+            } else {  // SQ4, (0,1)
+                const uint32_t *rq = rp + g.RW;
+                const uint32_t m1 = rm[j + 1];
+                const uint32_t p0 = rp[j], p1 = rp[j + 1], p2 = rp[j + 2];
+                const uint32_t q1 = rq[j + 1];
+                const uint32_t M0 = m1;
+                const uint32_t Pm = fsr(p0, p1, 31), P0 = p1, P1 = fsr(p1, p2, 1);
+                const uint32_t Q0 = q1;
+                ta = A0; tb = P0;
+                S = count6(eqm(A1, ta), eqm(Am, ta), eqm(M0, ta), eqm(P1, tb), eqm(Pm, tb),
+                           eqm(Q0, tb));
+            }
         }
-
         const uint32_t unl = (ta ^ tb) & am;
         const uint32_t dmask = unl & ge_const(S, g.draw_lo) & ~ge_const(S, g.draw_hi + 1);
         uint32_t acc = unl & ~dmask;
-        uint32_t dm = dmask;
-        while (dm) {
-            const int p = __ffs(dm) - 1;
-            dm &= dm - 1;
-            const uint32_t Sp = ((S.s0 >> p) & 1u) | (((S.s1 >> p) & 1u) << 1) |
-                                (((S.s2 >> p) & 1u) << 2) | (((S.s3 >> p) & 1u) << 3);
-            const uint32_t site = (uint32_t)(y * g.Lx + x0 + p);
-            const Philox4 r = philox4(site, (uint32_t)f, s_lo, s_hi, g.k0, g.k1);
-            if ((uint64_t)r.v[0] < thr[Sp]) acc |= 1u << p;
+
+        // Spread the warp's draws over its lanes: draw k (in lane order, then bit
+        // order) is done by lane k mod 32; accepted bits return through warp_acc.
+        const int nd = __popc(dmask);
+        int incl = nd;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+            if (lane >= o) incl += v;
         }
+        const int total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+        if (total > 0) {
+            const int excl = incl - nd;
+            const uint32_t site_base = (uint32_t)(y * g.Lx + x0);
+            for (int k0 = 0; k0 < total; k0 += 32) {
+                const int k = k0 + lane;
+                int owner = 0;
+#pragma unroll
+                for (int step = 16; step > 0; step >>= 1) {
+                    const int v = __shfl_sync(0xFFFFFFFFu, incl, owner + step - 1);
+                    if (v <= k) owner += step;
+                }
+                owner = min(owner, 31);
+                const int oex = __shfl_sync(0xFFFFFFFFu, excl, owner);
+                const uint32_t odm = __shfl_sync(0xFFFFFFFFu, dmask, owner);
+                const uint32_t os0 = __shfl_sync(0xFFFFFFFFu, S.s0, owner);
+                const uint32_t os1 = __shfl_sync(0xFFFFFFFFu, S.s1, owner);
+                const uint32_t os2 = __shfl_sync(0xFFFFFFFFu, S.s2, owner);
+                const uint32_t os3 = __shfl_sync(0xFFFFFFFFu, S.s3, owner);
+                const uint32_t obase = __shfl_sync(0xFFFFFFFFu, site_base, owner);
+                if (k < total) {
+                    const int p = (int)__fns(odm, 0u, k - oex + 1);
+                    const uint32_t Sp = ((os0 >> p) & 1u) | (((os1 >> p) & 1u) << 1) |
+                                        (((os2 >> p) & 1u) << 2) | (((os3 >> p) & 1u) << 3);
+                    const Philox4 r = philox4(obase + (uint32_t)p, (uint32_t)f, s_lo, s_hi, g.k0, g.k1);
+                    if ((uint64_t)r.v[0] < thr[Sp]) atomicOr(warp_acc + owner, 1u << p);
+                }
+            }
+            __syncwarp();
+            acc |= warp_acc[lane];
+            warp_acc[lane] = 0u;
+            __syncwarp();
+        }
+
         A.att += __popc(am);
         A.unl += __popc(unl);
-        A.drw += __popc(dmask);
+        A.drw += nd;
         if (acc) {
             const int na = __popc(acc);
             A.acc += na;
             const int sum_s = __popc(S.s0 & acc) + 2 * __popc(S.s1 & acc) +
                               4 * __popc(S.s2 & acc) + 8 * __popc(S.s3 & acc);
             A.dn += 2 * (sum_s - g.zm1 * na);
-            flip_sites(lat + (size_t)y * g.RW, g.RW, g.Lx, x0, acc);
-            int yb = y + bdy;
-            if (yb < 0) yb += g.Ly;
-            if (yb >= g.Ly) yb -= g.Ly;
-            flip_sites(lat + (size_t)yb * g.RW, g.RW, g.Lx, x0 + bdx, acc);
+            flip_global_row(g, y, x0, acc);
+            flip_global_row(g, y + bdy, x0 + bdx, acc);
         }
     }
 }
@@ -345,29 +456,59 @@ __device__ __forceinline__ T warp_sum(T v)
     return v;
 }
 
-__global__ void __launch_bounds__(kThreads, 1)
+__device__ __forceinline__ uint32_t cluster_nctarank()
+{
+    uint32_t v;
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(v));
+    return v;
+}
+
+__device__ __forceinline__ uint32_t cluster_ctarank()
+{
+    uint32_t v;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(v));
+    return v;
+}
+
+template <int THREADS>
+__global__ void __launch_bounds__(THREADS, 1)
 resident_sweep_kernel(const SweepJob *__restrict__ jobs, const SweepCall *__restrict__ calls,
                       const SweepJob job0, const SweepCall call0)
 {
+    constexpr int kWarps = THREADS / 32;
     extern __shared__ __align__(16) uint32_t lat[];
     __shared__ PhaseP pp[2][8];
     __shared__ uint64_t thr[16];
     __shared__ long long red[5][kWarps];
-    __shared__ long long running;
+    __shared__ uint32_t warp_acc_all[kWarps][32];
 
-    const SweepJob &J = jobs ? jobs[blockIdx.x] : job0;
-    const SweepCall C = calls ? calls[blockIdx.x] : call0;
-    if (C.n_mcs <= 0) return;
+    const int C = (int)cluster_nctarank();
+    const int rank = (int)cluster_ctarank();
+    const int job = (int)blockIdx.x / C;
+    const SweepJob &J = jobs ? jobs[job] : job0;
+    const SweepCall Cl = calls ? calls[job] : call0;
+    if (Cl.n_mcs <= 0) return;  // uniform over the cluster
 
     Geo g;
     g.Lx = J.Lx; g.Ly = J.Ly; g.W = J.W; g.RW = J.RW; g.magicW = J.magicW;
     g.k0 = J.key0; g.k1 = J.key1; g.draw_lo = J.draw_lo; g.draw_hi = J.draw_hi;
     g.zm1 = (J.geometry == kTRI6 ? 6 : 4) - 1;
+    g.C = C;
+    g.rank = rank;
+    g.Y0 = (int)(((long long)rank * g.Ly) / C);
+    g.Y1 = (int)(((long long)(rank + 1) * g.Ly) / C);
+    g.lat_addr = smem_addr(lat);
     const int tid = threadIdx.x;
+    const int NL = g.Y1 - g.Y0 + 4;
+    uint32_t *warp_acc = warp_acc_all[tid >> 5];
+    warp_acc[tid & 31] = 0u;
 
-    // Load the lattice into padded shared-memory rows.
-    for (int idx = tid; idx < g.Ly * g.RW; idx += kThreads) {
-        const int y = idx / g.RW, w = idx - y * g.RW;
+    // Load band and halo rows into padded shared-memory rows.
+    for (int idx = tid; idx < NL * g.RW; idx += THREADS) {
+        const int lr = idx / g.RW, w = idx - lr * g.RW;
+        int y = g.Y0 - 2 + lr;
+        y %= g.Ly;
+        if (y < 0) y += g.Ly;
         const int pos0 = 32 * w - 32;
         uint32_t v = 0u;
         if (J.packing == kPackBit && pos0 >= 0 && pos0 + 32 <= g.Lx) {
@@ -382,55 +523,62 @@ resident_sweep_kernel(const SweepJob *__restrict__ jobs, const SweepCall *__rest
         lat[idx] = v;
     }
     if (tid < 16) thr[tid] = J.thr[tid];
-    if (tid < 8) phase_params(J.geometry, g.Lx, g.Ly, g.W, g.k0, g.k1, C.sweep0, tid, &pp[0][tid]);
-    if (tid == 0) running = J.state[kNUnlike];
-    __syncthreads();
+    if (tid < 8)
+        phase_params(J.geometry, g.Lx, g.Ly, g.W, g.Y0, g.Y1, g.k0, g.k1, Cl.sweep0, tid, &pp[0][tid]);
+    // Every CTA of the cluster must be loaded before any peer flips into it.
+    if (C > 1) {
+        asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory");
+        asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+    } else {
+        __syncthreads();
+    }
 
+    // Start energy for the trace, read before any CTA of this lattice can finish.
+    const long long n_unlike0 = (tid == 0 && rank == 0 && Cl.trace_every > 0) ? J.state[kNUnlike] : 0;
     unsigned long long t_att = 0, t_unl = 0, t_drw = 0, t_acc = 0;
     long long t_dn = 0;
-    int dn_trace = 0;
-    for (long long it = 0; it < C.n_mcs; ++it) {
-        const long long s = C.sweep0 + it;
+    for (long long it = 0; it < Cl.n_mcs; ++it) {
+        const long long s = Cl.sweep0 + it;
         const uint32_t s_lo = (uint32_t)(unsigned long long)s;
         const uint32_t s_hi = (uint32_t)((unsigned long long)s >> 32);
         const int buf = (int)(it & 1);
         Acc A = {0u, 0u, 0u, 0u, 0};
         for (int f = 0; f < 8; ++f) {
-            if (f == 7 && tid < 8 && it + 1 < C.n_mcs)
-                phase_params(J.geometry, g.Lx, g.Ly, g.W, g.k0, g.k1, s + 1, tid, &pp[buf ^ 1][tid]);
+            if (f == 7 && tid < 8 && it + 1 < Cl.n_mcs)
+                phase_params(J.geometry, g.Lx, g.Ly, g.W, g.Y0, g.Y1, g.k0, g.k1, s + 1, tid,
+                             &pp[buf ^ 1][tid]);
             const PhaseP P = pp[buf][f];
             if (J.geometry == kTRI6) {
-                if (P.oi == 0) run_phase<kTRI6, 0>(lat, g, P, thr, f, s_lo, s_hi, A);
-                else if (P.oi == 1) run_phase<kTRI6, 1>(lat, g, P, thr, f, s_lo, s_hi, A);
-                else run_phase<kTRI6, 2>(lat, g, P, thr, f, s_lo, s_hi, A);
+                if (P.oi == 0) run_phase<kTRI6, 0, THREADS>(lat, g, P, thr, warp_acc, f, s_lo, s_hi, A);
+                else if (P.oi == 1) run_phase<kTRI6, 1, THREADS>(lat, g, P, thr, warp_acc, f, s_lo, s_hi, A);
+                else run_phase<kTRI6, 2, THREADS>(lat, g, P, thr, warp_acc, f, s_lo, s_hi, A);
             } else {
-                if (P.oi == 0) run_phase<kSQ4, 0>(lat, g, P, thr, f, s_lo, s_hi, A);
-                else run_phase<kSQ4, 1>(lat, g, P, thr, f, s_lo, s_hi, A);
+                if (P.oi == 0) run_phase<kSQ4, 0, THREADS>(lat, g, P, thr, warp_acc, f, s_lo, s_hi, A);
+                else run_phase<kSQ4, 1, THREADS>(lat, g, P, thr, warp_acc, f, s_lo, s_hi, A);
             }
-            __syncthreads();
+            phase_barrier(C);
         }
         t_att += A.att; t_unl += A.unl; t_drw += A.drw; t_acc += A.acc;
         t_dn += A.dn;
-        dn_trace += A.dn;
-        if (C.trace_every > 0 && C.trace != nullptr && (it + 1) % C.trace_every == 0) {
-            const int ws = warp_sum(dn_trace);
-            if ((tid & 31) == 0) red[0][tid >> 5] = ws;
-            dn_trace = 0;
-            __syncthreads();
-            if (tid == 0) {
-                long long sum = 0;
-                for (int w = 0; w < kWarps; ++w) sum += red[0][w];
-                running += sum;
-                C.trace[(it + 1) / C.trace_every - 1] = running;
-            }
-            __syncthreads();
+        // Energy trace: each CTA adds its cumulative dn; CTA 0 adds the start value
+        // (the launcher zeroes the trace buffer).
+        if (Cl.trace_every > 0 && (it + 1) % Cl.trace_every == 0) {
+            const long long ws = warp_sum(t_dn);
+            if ((tid & 31) == 0 && ws != 0)
+                atomicAdd((unsigned long long *)&Cl.trace[(it + 1) / Cl.trace_every - 1],
+                          (unsigned long long)ws);
+            if (tid == 0 && rank == 0)
+                atomicAdd((unsigned long long *)&Cl.trace[(it + 1) / Cl.trace_every - 1],
+                          (unsigned long long)n_unlike0);
         }
     }
 
-    // Write the lattice back (main positions only).
-    for (int idx = tid; idx < g.Ly * g.W; idx += kThreads) {
-        const int y = idx / g.W, w = idx - y * g.W;
-        const uint32_t v = lat[(size_t)y * g.RW + w + 1];
+    // Write the band back (main positions only).
+    const int H = g.Y1 - g.Y0;
+    for (int idx = tid; idx < H * g.W; idx += THREADS) {
+        const int r = idx / g.W, w = idx - r * g.W;
+        const int y = g.Y0 + r;
+        const uint32_t v = lat[(size_t)(r + 2) * g.RW + w + 1];
         const int pos0 = 32 * w;
         const int nvalid = min(32, g.Lx - pos0);
         if (J.packing == kPackBit) {
@@ -458,58 +606,103 @@ resident_sweep_kernel(const SweepJob *__restrict__ jobs, const SweepCall *__rest
     }
 }
 
-}  // namespace
+constexpr int kThreadsSingle = 1024;
+constexpr int kThreadsCluster = 256;
 
-size_t resident_smem_bytes(int Lx, int Ly)
+template <int THREADS>
+cudaError_t configure_once()
 {
-    const size_t RW = (size_t)(Lx + 127) / 32;
-    return RW * (size_t)Ly * sizeof(uint32_t);
-}
-
-int resident_max_smem_bytes()
-{
-    // Dynamic shared memory left after the kernel's static arrays.
-    return 227 * 1024 - 4096;
-}
-
-namespace {
-cudaError_t configure_resident()
-{
-    // Once per process and device use; setting the attribute again is harmless.
     static thread_local int configured_device = -1;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (configured_device == dev) return cudaSuccess;
-    e = cudaFuncSetAttribute(resident_sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             resident_max_smem_bytes());
+    e = cudaFuncSetAttribute(resident_sweep_kernel<THREADS>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, resident_max_smem_bytes());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(resident_sweep_kernel<THREADS>,
+                                 cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e == cudaSuccess) configured_device = dev;
     return e;
 }
+
+cudaError_t launch(const SweepJob *d_jobs, const SweepCall *d_calls, const SweepJob &job0,
+                   const SweepCall &call0, int n_jobs, int cluster, size_t smem_bytes,
+                   cudaStream_t stream)
+{
+    cudaLaunchConfig_t cfg;
+    memset(&cfg, 0, sizeof(cfg));
+    cfg.gridDim = dim3((unsigned)(n_jobs * cluster), 1, 1);
+    cfg.dynamicSmemBytes = smem_bytes;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)cluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t e;
+    if (cluster == 1) {
+        e = configure_once<kThreadsSingle>();
+        if (e != cudaSuccess) return e;
+        cfg.blockDim = dim3(kThreadsSingle, 1, 1);
+        e = cudaLaunchKernelEx(&cfg, resident_sweep_kernel<kThreadsSingle>, d_jobs, d_calls, job0, call0);
+    } else {
+        e = configure_once<kThreadsCluster>();
+        if (e != cudaSuccess) return e;
+        cfg.blockDim = dim3(kThreadsCluster, 1, 1);
+        e = cudaLaunchKernelEx(&cfg, resident_sweep_kernel<kThreadsCluster>, d_jobs, d_calls, job0, call0);
+    }
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
 }  // namespace
 
+size_t resident_smem_bytes(int Lx, int Ly, int cluster)
+{
+    const size_t RW = (size_t)(Lx + 127) / 32;
+    const int C = cluster < 1 ? 1 : cluster;
+    size_t H = 0;  // tallest band
+    for (int c = 0; c < C; ++c) {
+        const size_t h = (size_t)(((long long)(c + 1) * Ly) / C - ((long long)c * Ly) / C);
+        if (h > H) H = h;
+    }
+    return RW * (H + 4) * sizeof(uint32_t);
+}
+
+int resident_max_smem_bytes()
+{
+    // Dynamic shared memory left after the kernel's static arrays (about 6.2 KB at
+    // 1024 threads: phase tables, thresholds, reductions, per-warp draw results).
+    return 227 * 1024 - 6400;
+}
+
+int resident_threads(int cluster) { return cluster == 1 ? kThreadsSingle : kThreadsCluster; }
+
+int resident_max_cluster(int Ly)
+{
+    int c = 16;
+    while (c > 1 && Ly / c < 4) c >>= 1;
+    return c;
+}
+
 cudaError_t launch_resident_sweep(const SweepJob *d_jobs, const SweepCall *d_calls, int n_jobs,
-                                  size_t smem_bytes, cudaStream_t stream)
+                                  int cluster, size_t smem_bytes, cudaStream_t stream)
 {
     if (n_jobs <= 0) return cudaSuccess;
-    cudaError_t e = configure_resident();
-    if (e != cudaSuccess) return e;
     SweepJob none_job;
     SweepCall none_call;
     memset(&none_job, 0, sizeof(none_job));
     memset(&none_call, 0, sizeof(none_call));
-    resident_sweep_kernel<<<n_jobs, kThreads, smem_bytes, stream>>>(d_jobs, d_calls, none_job,
-                                                                     none_call);
-    return cudaGetLastError();
+    return launch(d_jobs, d_calls, none_job, none_call, n_jobs, cluster, smem_bytes, stream);
 }
 
-cudaError_t launch_resident_sweep_one(const SweepJob &job, const SweepCall &call, size_t smem_bytes,
-                                      cudaStream_t stream)
+cudaError_t launch_resident_sweep_one(const SweepJob &job, const SweepCall &call, int cluster,
+                                      size_t smem_bytes, cudaStream_t stream)
 {
-    cudaError_t e = configure_resident();
-    if (e != cudaSuccess) return e;
-    resident_sweep_kernel<<<1, kThreads, smem_bytes, stream>>>(nullptr, nullptr, job, call);
-    return cudaGetLastError();
+    return launch(nullptr, nullptr, job, call, 1, cluster, smem_bytes, stream);
 }
 
 }  // namespace klmc

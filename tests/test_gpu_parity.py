@@ -21,9 +21,9 @@ GEOMS = [klmc.TRI6, klmc.SQ4]
 PACKS = [klmc.PACK_BIT, klmc.PACK_BYTE]
 
 
-def make(Lx, Ly, nA, bw, seed, geometry=klmc.TRI6, packing=klmc.PACK_BIT):
+def make(Lx, Ly, nA, bw, seed, geometry=klmc.TRI6, packing=klmc.PACK_BIT, cluster=0):
     return klmc.Lattice(Lx, Ly, geometry=geometry, packing=packing, n_A=nA, omega_over_kT=bw,
-                        seed=seed)
+                        seed=seed, cluster=cluster)
 
 
 def assert_same_run(lat, ref):
@@ -68,6 +68,31 @@ def test_sweep_parity(geometry, Lx, Ly, nA, bw):
     lat.sweep(20)
     ref = oracle.run(Lx, Ly, geometry, bw, seed, t0, 0, 20)
     assert_same_run(lat, ref)
+
+
+@pytest.mark.parametrize("geometry", GEOMS)
+@pytest.mark.parametrize("cluster", [1, 2, 3, 4, 5, 8, 16])
+@pytest.mark.parametrize("Lx,Ly,nA,bw", [(64, 64, 2048, 0.6), (100, 101, 3030, 1.0), (37, 70, 700, -0.4),
+                                         (130, 131, 8000, 0.85)])
+def test_cluster_size_parity(geometry, cluster, Lx, Ly, nA, bw):
+    """The split of a lattice over a thread-block cluster never changes the result."""
+    if Ly // cluster < 4:
+        pytest.skip("bands need >= 4 rows")
+    seed = 77 + cluster
+    lat = make(Lx, Ly, nA, bw, seed, geometry, cluster=cluster)
+    tr = lat.sweep_traced(12, 4)
+    ref = oracle.run(Lx, Ly, geometry, bw, seed, oracle.init(Lx, Ly, nA, seed), 0, 12, trace_every=4)
+    assert_same_run(lat, ref)
+    torch.cuda.synchronize()
+    assert tr.cpu().numpy().tolist() == ref.trace.tolist()
+
+
+def test_cluster_size_rejected():
+    with pytest.raises(klmc.KlmcError) as e:
+        make(16, 16, 100, 0.5, 1, cluster=8)  # bands of 2 rows
+    assert e.value.status == 1
+    with pytest.raises(klmc.KlmcError):
+        make(64, 64, 100, 0.5, 1, cluster=17)
 
 
 @pytest.mark.parametrize("geometry", GEOMS)
@@ -122,6 +147,17 @@ def test_checkpoint_resume():
     assert np.array_equal(c.get_lattice(), ref.lattice)
     assert c.counters()["accepts"] == ref.accepts
     assert b.n_A == nA
+
+
+def test_set_lattice_device():
+    Lx, Ly, bw, seed = 45, 30, 0.8, 14
+    t = oracle.init(Lx, Ly, 700, 99)
+    lat = make(Lx, Ly, 10, bw, seed)
+    lat.set_lattice_device(torch.from_numpy(t).cuda(), 3)
+    assert lat.n_A == 700
+    lat.sweep(12)
+    ref = oracle.run(Lx, Ly, klmc.TRI6, bw, seed, t, 3, 12)
+    assert_same_run(lat, ref)
 
 
 def _hist_equal(lat, t, species):
@@ -198,16 +234,29 @@ def test_batch_parity_mixed():
     b.close()
 
 
-def test_largest_resident_lattice():
-    Lx = Ly = 1290
+def test_largest_single_cta_lattice():
+    """The largest lattice one CTA holds (1280 rows + 4 halo rows of 44 words)."""
+    Lx, Ly = 1280, 1280
     nA = Lx * Ly // 2
-    lat = make(Lx, Ly, nA, 0.85, 7)
+    lat = make(Lx, Ly, nA, 0.85, 7, cluster=1)
     lat.sweep(2)
     ref = oracle.run(Lx, Ly, klmc.TRI6, 0.85, 7, oracle.init(Lx, Ly, nA, 7), 0, 2)
     assert_same_run(lat, ref)
-    big = make(1400, 1400, 1000, 0.5, 1)
     with pytest.raises(klmc.KlmcError) as e:
-        big.sweep(1)
+        make(1400, 1400, 1000, 0.5, 1, cluster=1).sweep(1)
+    assert e.value.status == 1
+
+
+def test_large_lattice_on_full_cluster():
+    """2048 x 2048 split over 16 CTAs (the largest side of the serving workload)."""
+    Lx = Ly = 2048
+    nA = Lx * Ly * 3 // 10
+    lat = make(Lx, Ly, nA, 0.7, 9)
+    lat.sweep(1)
+    ref = oracle.run(Lx, Ly, klmc.TRI6, 0.7, 9, oracle.init(Lx, Ly, nA, 9), 0, 1)
+    assert_same_run(lat, ref)
+    with pytest.raises(klmc.KlmcError) as e:
+        make(6000, 6000, 1000, 0.5, 1).sweep(1)
     assert e.value.status == 1
 
 
