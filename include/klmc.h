@@ -139,6 +139,32 @@ klmc_status klmc_cluster_histogram_device(klmc_ctx *c, int32_t species, int64_t 
                                           int64_t *dev_counts, int64_t capacity,
                                           int64_t *dev_n_distinct);
 
+/* Largest lattice, in sites, accepted by klmc_cluster_histogram_noalloc. */
+#define KLMC_NOALLOC_MAX_SITES (1 << 20)
+
+/* The cluster-size histogram of klmc_cluster_histogram_device for a caller-owned
+ * lattice, without allocating any device memory.  The paper has no counterpart:
+ * this entry point exists for callers that cannot call cudaMalloc, such as a host
+ * framework that owns all device memory under a fixed budget with no allocator
+ * hook, or a latency-bound loop that cannot accept cudaMalloc's implicit device
+ * synchronisation.
+ *  dev_lattice  device lattice, Ly rows of `pitch` 32-bit words (KLMC_PACK_BIT,
+ *               site x is bit x%32 of word x/32) or `pitch` bytes (KLMC_PACK_BYTE,
+ *               1 = A); owned by the caller, read only.
+ *  outputs      as klmc_cluster_histogram_device (caller device buffers).
+ *  stream       cudaStream_t the work is enqueued on; returns without waiting.
+ * Scratch comes from one fixed device array of the library (about 12.6 MB, held by
+ * every GPU that loads the library until the process exits), shared by all calls:
+ * calls whose work overlaps on the GPU race and must be serialised by the caller.
+ * The first call on each device resolves the array's device address (set-up) and
+ * should come before any stream capture on that device.  EINVAL when Lx*Ly
+ * exceeds KLMC_NOALLOC_MAX_SITES or an argument is invalid. */
+klmc_status klmc_cluster_histogram_noalloc(const void *dev_lattice, int32_t packing, int32_t Lx,
+                                           int32_t Ly, int32_t pitch, int32_t geometry,
+                                           int32_t species, int64_t *dev_sizes,
+                                           int64_t *dev_counts, int64_t capacity,
+                                           int64_t *dev_n_distinct, void *stream);
+
 /* Counters (see klmc_counters).  Synchronises. */
 klmc_status klmc_get_counters(klmc_ctx *c, klmc_counters *out);
 

@@ -55,6 +55,8 @@ bool device_ok(std::string *why)
 
 }  // namespace
 
+void klmc::set_last_error(const char *msg) { g_err = msg ? msg : ""; }
+
 struct klmc_ctx {
     klmc_params p;
     long long N = 0, nA = 0;

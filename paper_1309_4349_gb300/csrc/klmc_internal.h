@@ -99,4 +99,7 @@ cudaError_t launch_cluster_histogram(const void *lat, int packing, int Lx, int L
                                      long long *sizes, long long *counts, long long capacity,
                                      long long *n_distinct, cudaStream_t stream);
 
+// Sets the message returned by klmc_last_error() on the calling thread.
+void set_last_error(const char *msg);
+
 }  // namespace klmc
