@@ -242,7 +242,7 @@ klmc_status create_one(klmc_ctx **out, const klmc_params *p, klmc_batch *owner)
     J.packing = c->p.packing;
     J.geometry = p->geometry;
     J.W = c->W;
-    J.RW = (p->Lx + 127) / 32;
+    J.RW = (p->Lx + 95) / 32;  // ceil(Lx / 32) + 2: windows read words j .. j+2
     J.magicW = (0x100000000ull + (unsigned long long)c->W - 1) / (unsigned long long)c->W;
     J.key0 = (uint32_t)p->seed;
     J.key1 = (uint32_t)(p->seed >> 32);

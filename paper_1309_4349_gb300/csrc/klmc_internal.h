@@ -32,7 +32,7 @@ struct SweepJob {
     int32_t packing;      // kPackBit / kPackByte
     int32_t geometry;     // kTRI6 / kSQ4
     int32_t W;            // 32-site words per row = ceil(Lx / 32)
-    int32_t RW;           // padded shared-memory row length in words
+    int32_t RW;           // padded shared-memory row length in words (W + 2)
     uint32_t key0, key1;  // Philox key = seed
     uint64_t magicW;      // ceil(2^32 / W): task t -> row (t * magicW) >> 32
     int32_t draw_lo;      // neighbour-agreement sums S in [draw_lo, draw_hi] need a draw

@@ -14,9 +14,11 @@
 // a cluster barrier (release/acquire), so the next phase sees every flip.
 //
 // Row layout.  A shared-memory row is RW 32-bit words holding the padded bit
-// positions pos in [-32, 32*RW - 32); position pos holds site (pos mod Lx).  All
-// copies are kept equal, so the 32-site window starting at any x in [-32, Lx + 32]
-// is one funnel shift of two words.
+// positions pos in [-32, 32*RW - 32); when loaded, position pos holds site
+// (pos mod Lx), so the 32-site window starting at any x in [-32, Lx + 32] is one
+// funnel shift of two words.  The windows of anchors x < Lx read only positions
+// -1 .. Lx+1, so flips keep exactly the copies at -1 (site Lx-1) and Lx, Lx+1
+// (sites 0, 1) equal to their sites; other pad positions are never read.
 //
 // Evaluation.  One thread handles the anchors of one 32-site word of one anchor
 // row.  Neighbour comparisons of all 32 positions are bitwise operations summed by
@@ -24,8 +26,9 @@
 // other than b, equal to a, plus neighbours of b, other than a, equal to b).  An
 // exchange changes the number of unlike contacts by dn = 2 (S - (z - 1)).  Unlike
 // pairs whose S lies in the draw range draw a Philox number; the rest are accepted
-// outright (Metropolis acceptance min{1, exp(-omega dn / kT)}, steps a-c).  The
-// draws of a warp are spread evenly over its 32 lanes before Philox runs.
+// outright (Metropolis acceptance min{1, exp(-omega dn / kT)}, steps a-c).  A
+// lane draws for its own anchors, two Philox evaluations interleaved at a time:
+// a phase is short, so its cost is the latency of its slowest task.
 #include <string.h>
 
 #include "klmc_internal.h"
@@ -64,6 +67,32 @@ __device__ __forceinline__ Philox4 philox4(uint32_t c0, uint32_t c1, uint32_t c2
     Philox4 out;
     out.v[0] = c0; out.v[1] = c1; out.v[2] = c2; out.v[3] = c3;
     return out;
+}
+
+// Word 0 of Philox4x32-10 for two counters that differ only in word 0, computed
+// in lockstep so the two dependency chains overlap.
+__device__ __forceinline__ void philox2_w0(uint32_t a0, uint32_t b0, uint32_t c1, uint32_t c2,
+                                           uint32_t c3, uint32_t k0, uint32_t k1, uint32_t &ra,
+                                           uint32_t &rb)
+{
+    uint32_t a1 = c1, a2 = c2, a3 = c3, b1 = c1, b2 = c2, b3 = c3;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const unsigned long long pa0 = (unsigned long long)a0 * 0xD2511F53ull;
+        const unsigned long long pa1 = (unsigned long long)a2 * 0xCD9E8D57ull;
+        const unsigned long long pb0 = (unsigned long long)b0 * 0xD2511F53ull;
+        const unsigned long long pb1 = (unsigned long long)b2 * 0xCD9E8D57ull;
+        const uint32_t na0 = (uint32_t)(pa1 >> 32) ^ a1 ^ k0;
+        const uint32_t na2 = (uint32_t)(pa0 >> 32) ^ a3 ^ k1;
+        const uint32_t nb0 = (uint32_t)(pb1 >> 32) ^ b1 ^ k0;
+        const uint32_t nb2 = (uint32_t)(pb0 >> 32) ^ b3 ^ k1;
+        a1 = (uint32_t)pa1; a3 = (uint32_t)pa0; a0 = na0; a2 = na2;
+        b1 = (uint32_t)pb1; b3 = (uint32_t)pb0; b0 = nb0; b2 = nb2;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    ra = a0;
+    rb = b0;
 }
 
 __device__ __forceinline__ int floor_div(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
@@ -117,7 +146,9 @@ __device__ __forceinline__ uint32_t anchor_mask(int x0, const PhaseP &P, int Lx)
 {
     const uint32_t rep = P.px == 4 ? 0x11111111u : 0x55555555u;
     const int pm = P.px - 1;
-    uint32_t m = (rep << ((P.rx - x0) & pm)) & range_mask(P.rx, min(P.rx + P.umax, Lx - 1), x0);
+    const int hi1 = min(P.rx + P.umax, Lx - 1);
+    if (x0 >= P.rx && x0 + 31 <= hi1) return rep << ((P.rx - x0) & pm);  // whole word in range
+    uint32_t m = (rep << ((P.rx - x0) & pm)) & range_mask(P.rx, hi1, x0);
     const int hi2 = min(P.rx - 1, P.rx + P.umax - Lx);  // wrapped part of the anchor row
     if (hi2 >= 0) m |= (rep << ((P.rx - Lx - x0) & pm)) & range_mask(0, hi2, x0);
     return m;
@@ -177,26 +208,23 @@ __device__ __forceinline__ Planes count6(uint32_t e0, uint32_t e1, uint32_t e2, 
     return P;
 }
 
-// Positions with S >= c (c uniform).
-__device__ __forceinline__ uint32_t ge_const(const Planes &S, int c)
-{
-    if (c <= 0) return 0xFFFFFFFFu;
-    if (c >= 16) return 0u;
-    const uint32_t sb[4] = {S.s0, S.s1, S.s2, S.s3};
-    uint32_t lt = 0u, eq = 0xFFFFFFFFu;
-#pragma unroll
-    for (int b = 3; b >= 0; --b) {
-        if ((c >> b) & 1) {
-            lt |= eq & ~sb[b];
-            eq &= sb[b];
-        } else {
-            eq &= ~sb[b];
-        }
-    }
-    return ~lt;
-}
-
 __device__ __forceinline__ uint32_t eqm(uint32_t v, uint32_t t) { return ~(v ^ t); }
+
+// Positions that need a draw: the exchange raises the energy when omega > 0
+// (sign > 0: S > z - 1) or lowers it when omega < 0 (sign < 0: S < z - 1).
+template <int G>
+__device__ __forceinline__ uint32_t draw_positions(const Planes &S, int sign)
+{
+    uint32_t up, down;
+    if (G == kTRI6) {  // z - 1 = 5, S in 0..10
+        up = S.s3 | (S.s2 & S.s1);                     // S >= 6
+        down = ~(S.s3 | (S.s2 & (S.s1 | S.s0)));       // S <= 4
+    } else {           // z - 1 = 3, S in 0..6
+        up = S.s2;                                     // S >= 4
+        down = ~(S.s2 | (S.s1 & S.s0));                // S <= 2
+    }
+    return sign > 0 ? up : (sign < 0 ? down : 0u);
+}
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p)
 {
@@ -230,59 +258,63 @@ __device__ __forceinline__ void xor_at(uint32_t row, int RW, int q, uint32_t mas
     if (s != 0 && w + 1 < RW) xor_word(row + 4u * (w + 1), rank, local, mask >> (32 - s));
 }
 
-// Flip the sites at positions pos + p (mask bit p) in one row copy, every padded copy.
-__device__ __forceinline__ void flip_row(uint32_t row, int RW, int Lx, int pos, uint32_t mask,
-                                         uint32_t rank, bool local)
-{
-    const int q = pos + 32;
-    for (int qq = q; qq > -32; qq -= Lx) xor_at(row, RW, qq, mask, rank, local);
-    for (int qq = q + Lx; qq < 32 * RW; qq += Lx) xor_at(row, RW, qq, mask, rank, local);
-}
-
-struct Geo {
-    int Lx, Ly, W, RW;
-    unsigned long long magicW;
-    uint32_t k0, k1;
-    int draw_lo, draw_hi;
-    int zm1;
-    int C, rank, Y0, Y1;
-    uint32_t lat_addr;  // shared address of local row 0
-};
-
 struct Acc {
     uint32_t att, unl, drw, acc;
     int32_t dn;
 };
 
-// Flip global row r (unwrapped, in [Y0 - 1, Y1]) in every CTA that holds a copy.
-__device__ __forceinline__ void flip_global_row(const Geo &g, int r, int pos, uint32_t mask)
+struct Geo {
+    int Lx, Ly, W, RW;
+    unsigned long long magicW;
+    uint32_t k0, k1;
+    int sign;            // draw when the exchange raises (+1) / lowers (-1) E; 0: never
+    int zm1;
+    int C, rank, Y0, Y1;
+    int prevY, prevH;    // band of CTA rank-1 (mod C)
+    int nextY, nextH;    // band of CTA rank+1 (mod C)
+    uint32_t lat_addr;   // shared address of local row 0
+};
+
+// Flip, in one copy of a row, the sites x0 + i (bit i of m, x0 = 32 j, every site
+// < Lx), and the pad copies that windows read: position -1 (site Lx-1) and
+// positions Lx, Lx+1 (sites 0, 1).
+__device__ __forceinline__ void flip_row(const Geo &g, uint32_t row, int j, unsigned long long m,
+                                         uint32_t rank, bool local)
+{
+    const uint32_t lo = (uint32_t)m, hi = (uint32_t)(m >> 32);
+    xor_word(row + 4u * (uint32_t)(j + 1), rank, local, lo);
+    xor_word(row + 4u * (uint32_t)(j + 2), rank, local, hi);
+    if (j == 0 && (lo & 3u)) xor_at(row, g.RW, g.Lx + 32, lo & 3u, rank, local);
+    const int b = g.Lx - 1 - 32 * j;
+    if (b >= 0 && b < 64 && ((m >> b) & 1ull)) xor_word(row, rank, local, 0x80000000u);
+}
+
+// Flip sites of global row r (unwrapped, in [Y0 - 1, Y1]) in every CTA holding a copy.
+__device__ __forceinline__ void flip_global_row(const Geo &g, int r, int j, unsigned long long m)
 {
     const int lr_self = r - g.Y0 + 2;
-    if (g.C == 1) {
-        // Rows 0, 1 and Ly-2, Ly-1 also live in the opposite halo.
-        const int gr = r < 0 ? r + g.Ly : (r >= g.Ly ? r - g.Ly : r);
-        for (int lr = gr + 2 >= g.Ly ? gr + 2 - g.Ly : gr + 2; lr < g.Ly + 4; lr += g.Ly)
-            flip_row(g.lat_addr + 4u * (uint32_t)(lr * g.RW), g.RW, g.Lx, pos, mask, 0u, true);
-        return;
-    }
-    if (lr_self >= 4 && lr_self < g.Y1 - g.Y0) {  // interior row: only the local copy
-        flip_row(g.lat_addr + 4u * (uint32_t)(lr_self * g.RW), g.RW, g.Lx, pos, mask, 0u, true);
+    const uint32_t rowbytes = 4u * (uint32_t)g.RW;
+    if (g.C > 1 && lr_self >= 4 && lr_self < g.Y1 - g.Y0) {  // interior row: local copy only
+        flip_row(g, g.lat_addr + rowbytes * (uint32_t)lr_self, j, m, 0u, true);
         return;
     }
     const int gr = r < 0 ? r + g.Ly : (r >= g.Ly ? r - g.Ly : r);
-    const int cand[3] = {g.rank == 0 ? g.C - 1 : g.rank - 1, g.rank,
-                         g.rank + 1 == g.C ? 0 : g.rank + 1};
+    if (g.C == 1) {  // rows 0, 1 and Ly-2, Ly-1 also live in the opposite halo
+        for (int lr = gr + 2 >= g.Ly ? gr + 2 - g.Ly : gr + 2; lr < g.Ly + 4; lr += g.Ly)
+            flip_row(g, g.lat_addr + rowbytes * (uint32_t)lr, j, m, 0u, true);
+        return;
+    }
     for (int k = 0; k < 3; ++k) {
-        const int d = cand[k];
-        if (k == 2 && d == cand[0]) break;  // C == 2: both neighbours are the same CTA
-        const int Yd = (int)(((long long)d * g.Ly) / g.C);
-        const int Hd = (int)(((long long)(d + 1) * g.Ly) / g.C) - Yd;
+        if (k == 2 && g.C == 2) break;  // both neighbours are the same CTA
+        const int d = k == 0 ? (g.rank == 0 ? g.C - 1 : g.rank - 1)
+                             : (k == 1 ? g.rank : (g.rank + 1 == g.C ? 0 : g.rank + 1));
+        const int Yd = k == 0 ? g.prevY : (k == 1 ? g.Y0 : g.nextY);
+        const int Hd = k == 0 ? g.prevH : (k == 1 ? g.Y1 - g.Y0 : g.nextH);
         int lr = gr - Yd + 2;
-        lr %= g.Ly;
         if (lr < 0) lr += g.Ly;
+        if (lr >= g.Ly) lr -= g.Ly;
         for (; lr < Hd + 4; lr += g.Ly)
-            flip_row(g.lat_addr + 4u * (uint32_t)(lr * g.RW), g.RW, g.Lx, pos, mask, (uint32_t)d,
-                     d == g.rank);
+            flip_row(g, g.lat_addr + rowbytes * (uint32_t)lr, j, m, (uint32_t)d, d == g.rank);
     }
 }
 
@@ -296,11 +328,10 @@ __device__ __forceinline__ void phase_barrier(int C)
     }
 }
 
-// One phase of one band.  Every task is (anchor row, word j).  The task loop runs
-// in whole warps so that a warp's draws can be redistributed over its lanes.
+// One phase of one band.  Every task is (anchor row, word j).
 template <int G, int OI, int THREADS>
 __device__ __forceinline__ void run_phase(const uint32_t *lat, const Geo &g, const PhaseP &P,
-                                          const uint64_t *thr, uint32_t *warp_acc, int f,
+                                          const uint64_t *thr, int f,
                                           uint32_t s_lo, uint32_t s_hi, Acc &A)
 {
     // b = a + o: (1,0) -> same row, +1; (0,1) -> next row; (1,-1) -> previous row, +1
@@ -378,51 +409,28 @@ __device__ __forceinline__ void run_phase(const uint32_t *lat, const Geo &g, con
             }
         }
         const uint32_t unl = (ta ^ tb) & am;
-        const uint32_t dmask = unl & ge_const(S, g.draw_lo) & ~ge_const(S, g.draw_hi + 1);
+        const uint32_t dmask = unl & draw_positions<G>(S, g.sign);
         uint32_t acc = unl & ~dmask;
 
-        // Spread the warp's draws over its lanes: draw k (in lane order, then bit
-        // order) is done by lane k mod 32; accepted bits return through warp_acc.
+        // Each lane draws for its own anchors, two Philox evaluations at a time.
+        const uint32_t site_base = (uint32_t)(y * g.Lx + x0);
+        uint32_t dm = dmask;
+        while (dm != 0u) {
+            const int p1 = __ffs(dm) - 1;
+            dm &= dm - 1u;
+            const int p2 = dm != 0u ? __ffs(dm) - 1 : p1;  // an odd last draw is repeated
+            dm &= dm - 1u;
+            uint32_t r1, r2;
+            philox2_w0(site_base + (uint32_t)p1, site_base + (uint32_t)p2, (uint32_t)f, s_lo, s_hi,
+                       g.k0, g.k1, r1, r2);
+            const uint32_t S1 = ((S.s0 >> p1) & 1u) | (((S.s1 >> p1) & 1u) << 1) |
+                                (((S.s2 >> p1) & 1u) << 2) | (((S.s3 >> p1) & 1u) << 3);
+            const uint32_t S2 = ((S.s0 >> p2) & 1u) | (((S.s1 >> p2) & 1u) << 1) |
+                                (((S.s2 >> p2) & 1u) << 2) | (((S.s3 >> p2) & 1u) << 3);
+            if ((uint64_t)r1 < thr[S1]) acc |= 1u << p1;
+            if ((uint64_t)r2 < thr[S2]) acc |= 1u << p2;
+        }
         const int nd = __popc(dmask);
-        int incl = nd;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int v = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-            if (lane >= o) incl += v;
-        }
-        const int total = __shfl_sync(0xFFFFFFFFu, incl, 31);
-        if (total > 0) {
-            const int excl = incl - nd;
-            const uint32_t site_base = (uint32_t)(y * g.Lx + x0);
-            for (int k0 = 0; k0 < total; k0 += 32) {
-                const int k = k0 + lane;
-                int owner = 0;
-#pragma unroll
-                for (int step = 16; step > 0; step >>= 1) {
-                    const int v = __shfl_sync(0xFFFFFFFFu, incl, owner + step - 1);
-                    if (v <= k) owner += step;
-                }
-                owner = min(owner, 31);
-                const int oex = __shfl_sync(0xFFFFFFFFu, excl, owner);
-                const uint32_t odm = __shfl_sync(0xFFFFFFFFu, dmask, owner);
-                const uint32_t os0 = __shfl_sync(0xFFFFFFFFu, S.s0, owner);
-                const uint32_t os1 = __shfl_sync(0xFFFFFFFFu, S.s1, owner);
-                const uint32_t os2 = __shfl_sync(0xFFFFFFFFu, S.s2, owner);
-                const uint32_t os3 = __shfl_sync(0xFFFFFFFFu, S.s3, owner);
-                const uint32_t obase = __shfl_sync(0xFFFFFFFFu, site_base, owner);
-                if (k < total) {
-                    const int p = (int)__fns(odm, 0u, k - oex + 1);
-                    const uint32_t Sp = ((os0 >> p) & 1u) | (((os1 >> p) & 1u) << 1) |
-                                        (((os2 >> p) & 1u) << 2) | (((os3 >> p) & 1u) << 3);
-                    const Philox4 r = philox4(obase + (uint32_t)p, (uint32_t)f, s_lo, s_hi, g.k0, g.k1);
-                    if ((uint64_t)r.v[0] < thr[Sp]) atomicOr(warp_acc + owner, 1u << p);
-                }
-            }
-            __syncwarp();
-            acc |= warp_acc[lane];
-            warp_acc[lane] = 0u;
-            __syncwarp();
-        }
 
         A.att += __popc(am);
         A.unl += __popc(unl);
@@ -433,8 +441,24 @@ __device__ __forceinline__ void run_phase(const uint32_t *lat, const Geo &g, con
             const int sum_s = __popc(S.s0 & acc) + 2 * __popc(S.s1 & acc) +
                               4 * __popc(S.s2 & acc) + 8 * __popc(S.s3 & acc);
             A.dn += 2 * (sum_s - g.zm1 * na);
-            flip_global_row(g, y, x0, acc);
-            flip_global_row(g, y + bdy, x0 + bdx, acc);
+            const int j = x0 >> 5;
+            // b sites; with bdx = 1 the pair of anchor Lx-1 wraps to site 0.
+            unsigned long long mb = (unsigned long long)acc << bdx;
+            bool wrap0 = false;
+            if (bdx == 1) {
+                const int wb = g.Lx - x0;
+                if (wb <= 32 && ((mb >> wb) & 1ull)) {
+                    mb &= ~(1ull << wb);
+                    wrap0 = true;
+                }
+            }
+            if (bdy == 0) {
+                flip_global_row(g, y, j, (unsigned long long)acc | mb);
+            } else {
+                flip_global_row(g, y, j, (unsigned long long)acc);
+                flip_global_row(g, y + bdy, j, mb);
+            }
+            if (wrap0) flip_global_row(g, y + bdy, 0, 1ull);
         }
     }
 }
@@ -480,7 +504,6 @@ resident_sweep_kernel(const SweepJob *__restrict__ jobs, const SweepCall *__rest
     __shared__ PhaseP pp[2][8];
     __shared__ uint64_t thr[16];
     __shared__ long long red[5][kWarps];
-    __shared__ uint32_t warp_acc_all[kWarps][32];
 
     const int C = (int)cluster_nctarank();
     const int rank = (int)cluster_ctarank();
@@ -491,17 +514,24 @@ resident_sweep_kernel(const SweepJob *__restrict__ jobs, const SweepCall *__rest
 
     Geo g;
     g.Lx = J.Lx; g.Ly = J.Ly; g.W = J.W; g.RW = J.RW; g.magicW = J.magicW;
-    g.k0 = J.key0; g.k1 = J.key1; g.draw_lo = J.draw_lo; g.draw_hi = J.draw_hi;
+    g.k0 = J.key0; g.k1 = J.key1;
     g.zm1 = (J.geometry == kTRI6 ? 6 : 4) - 1;
+    // The host's draw range is [z, 2(z-1)] (omega > 0), [0, z-2] (omega < 0) or empty.
+    g.sign = J.draw_lo > J.draw_hi ? 0 : (J.draw_lo == 0 ? -1 : 1);
     g.C = C;
     g.rank = rank;
     g.Y0 = (int)(((long long)rank * g.Ly) / C);
     g.Y1 = (int)(((long long)(rank + 1) * g.Ly) / C);
+    {
+        const int pr = rank == 0 ? C - 1 : rank - 1, nr = rank + 1 == C ? 0 : rank + 1;
+        g.prevY = (int)(((long long)pr * g.Ly) / C);
+        g.prevH = (int)(((long long)(pr + 1) * g.Ly) / C) - g.prevY;
+        g.nextY = (int)(((long long)nr * g.Ly) / C);
+        g.nextH = (int)(((long long)(nr + 1) * g.Ly) / C) - g.nextY;
+    }
     g.lat_addr = smem_addr(lat);
     const int tid = threadIdx.x;
     const int NL = g.Y1 - g.Y0 + 4;
-    uint32_t *warp_acc = warp_acc_all[tid >> 5];
-    warp_acc[tid & 31] = 0u;
 
     // Load band and halo rows into padded shared-memory rows.
     for (int idx = tid; idx < NL * g.RW; idx += THREADS) {
@@ -549,12 +579,12 @@ resident_sweep_kernel(const SweepJob *__restrict__ jobs, const SweepCall *__rest
                              &pp[buf ^ 1][tid]);
             const PhaseP P = pp[buf][f];
             if (J.geometry == kTRI6) {
-                if (P.oi == 0) run_phase<kTRI6, 0, THREADS>(lat, g, P, thr, warp_acc, f, s_lo, s_hi, A);
-                else if (P.oi == 1) run_phase<kTRI6, 1, THREADS>(lat, g, P, thr, warp_acc, f, s_lo, s_hi, A);
-                else run_phase<kTRI6, 2, THREADS>(lat, g, P, thr, warp_acc, f, s_lo, s_hi, A);
+                if (P.oi == 0) run_phase<kTRI6, 0, THREADS>(lat, g, P, thr, f, s_lo, s_hi, A);
+                else if (P.oi == 1) run_phase<kTRI6, 1, THREADS>(lat, g, P, thr, f, s_lo, s_hi, A);
+                else run_phase<kTRI6, 2, THREADS>(lat, g, P, thr, f, s_lo, s_hi, A);
             } else {
-                if (P.oi == 0) run_phase<kSQ4, 0, THREADS>(lat, g, P, thr, warp_acc, f, s_lo, s_hi, A);
-                else run_phase<kSQ4, 1, THREADS>(lat, g, P, thr, warp_acc, f, s_lo, s_hi, A);
+                if (P.oi == 0) run_phase<kSQ4, 0, THREADS>(lat, g, P, thr, f, s_lo, s_hi, A);
+                else run_phase<kSQ4, 1, THREADS>(lat, g, P, thr, f, s_lo, s_hi, A);
             }
             phase_barrier(C);
         }
@@ -606,7 +636,7 @@ resident_sweep_kernel(const SweepJob *__restrict__ jobs, const SweepCall *__rest
     }
 }
 
-constexpr int kThreadsSingle = 1024;
+constexpr int kThreadsSingle = 512;
 constexpr int kThreadsCluster = 256;
 
 template <int THREADS>
@@ -662,7 +692,7 @@ cudaError_t launch(const SweepJob *d_jobs, const SweepCall *d_calls, const Sweep
 
 size_t resident_smem_bytes(int Lx, int Ly, int cluster)
 {
-    const size_t RW = (size_t)(Lx + 127) / 32;
+    const size_t RW = (size_t)(Lx + 95) / 32;  // ceil(Lx / 32) + 2
     const int C = cluster < 1 ? 1 : cluster;
     size_t H = 0;  // tallest band
     for (int c = 0; c < C; ++c) {
@@ -674,9 +704,9 @@ size_t resident_smem_bytes(int Lx, int Ly, int cluster)
 
 int resident_max_smem_bytes()
 {
-    // Dynamic shared memory left after the kernel's static arrays (about 6.2 KB at
-    // 1024 threads: phase tables, thresholds, reductions, per-warp draw results).
-    return 227 * 1024 - 6400;
+    // Dynamic shared memory left after the kernel's static arrays (about 2.2 KB at
+    // 1024 threads: phase tables, thresholds, reductions).
+    return 227 * 1024 - 3072;
 }
 
 int resident_threads(int cluster) { return cluster == 1 ? kThreadsSingle : kThreadsCluster; }
