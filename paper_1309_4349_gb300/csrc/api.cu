@@ -3,6 +3,7 @@
 #include <math.h>
 #include <string.h>
 
+#include <map>
 #include <new>
 #include <string>
 #include <utility>
@@ -77,6 +78,10 @@ struct klmc_ctx {
     uint8_t *dbytes = nullptr;    // lazily: one byte per site
     klmc_batch *owner = nullptr;  // non-null for replica views
     std::vector<std::pair<void *, size_t>> allocs;
+    // tiled path: band height, capture stream, and instantiated graphs of K sweeps
+    int tiled_H = 0;
+    cudaStream_t capture_stream = nullptr;
+    std::map<int, cudaGraphExec_t> graphs;
 };
 
 struct klmc_batch {
@@ -106,6 +111,10 @@ void *dev_alloc(klmc_ctx *c, size_t bytes)
 
 void free_all(klmc_ctx *c)
 {
+    for (auto &g : c->graphs) cudaGraphExecDestroy(g.second);
+    c->graphs.clear();
+    if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
+    c->capture_stream = nullptr;
     for (auto &a : c->allocs) {
         if (c->p.alloc && c->p.free) c->p.free(a.first, a.second, c->p.stream, c->p.user);
         else if (!c->p.alloc) cudaFreeAsync(a.first, c->stream);
@@ -129,7 +138,7 @@ klmc_status validate(const klmc_params *p)
         return fail(KLMC_EINVAL, "fraction_A must be in [0, 1]");
     if (p->n_A > N) return fail(KLMC_EINVAL, "n_A must be in [0, Lx*Ly]");
     if (p->alloc && !p->free) return fail(KLMC_EINVAL, "alloc given without free");
-    if (p->cluster < 0 || p->cluster > 16) return fail(KLMC_EINVAL, "cluster must be in [0, 16]");
+    if (p->cluster < -1 || p->cluster > 16) return fail(KLMC_EINVAL, "cluster must be in [-1, 16]");
     if (p->cluster > 1 && p->Ly / p->cluster < 4)
         return fail(KLMC_EINVAL, "cluster too large: every band needs >= 4 rows");
     return KLMC_OK;
@@ -217,7 +226,10 @@ klmc_status create_one(klmc_ctx **out, const klmc_params *p, klmc_batch *owner)
     c->N = (long long)p->Lx * p->Ly;
     c->nA = p->n_A >= 0 ? p->n_A : (long long)floor(p->fraction_A * (double)c->N + 0.5);
     c->W = (p->Lx + 31) / 32;
-    c->cluster = p->cluster > 0 ? p->cluster : auto_cluster(p->Lx, p->Ly);
+    c->cluster = p->cluster != 0 ? p->cluster : auto_cluster(p->Lx, p->Ly);
+    if (p->cluster == 0 &&
+        resident_smem_bytes(p->Lx, p->Ly, c->cluster) > (size_t)resident_max_smem_bytes())
+        c->cluster = -1;  // automatic choice, too large for shared memory: tiled path
     if (c->p.packing == KLMC_PACK_BIT) {
         c->pitch = (c->W + 3) / 4 * 4;  // 16-byte rows
         c->lat_bytes = (size_t)c->pitch * 4 * p->Ly;
@@ -280,6 +292,70 @@ klmc_status check_resident(const klmc_ctx *c, int cluster)
     return KLMC_OK;
 }
 
+// Instantiated graph of K sweeps on the tiled path (8 K phase launches, then
+// state[kSweepBase] += K), built once per handle and K on a private capture stream.
+klmc_status tiled_graph(klmc_ctx *c, int K, cudaGraphExec_t *out)
+{
+    auto it = c->graphs.find(K);
+    if (it != c->graphs.end()) {
+        *out = it->second;
+        return KLMC_OK;
+    }
+    if (!c->capture_stream)
+        KLMC_CUDA(cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking));
+    cudaGraph_t graph = nullptr;
+    KLMC_CUDA(cudaStreamBeginCapture(c->capture_stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = launch_tiled_phases(c->job, c->tiled_H, 0, K, c->capture_stream);
+    if (e == cudaSuccess) e = launch_advance(c->state, K, c->capture_stream);
+    cudaError_t e2 = cudaStreamEndCapture(c->capture_stream, &graph);
+    if (e == cudaSuccess) e = e2;
+    cudaGraphExec_t exec = nullptr;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return fail(KLMC_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    c->graphs[K] = exec;
+    *out = exec;
+    return KLMC_OK;
+}
+
+// n_mcs sweeps on the tiled path: graph replays of K sweeps, direct launches for
+// the rest, the trace kernel after every trace_every-th sweep.
+klmc_status sweep_tiled(klmc_ctx *c, int64_t n_mcs, int64_t trace_every, int64_t *dev_trace)
+{
+    if (c->tiled_H == 0) {
+        int dev = 0, sms = 0;
+        KLMC_CUDA(cudaGetDevice(&dev));
+        KLMC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        c->tiled_H = tiled_band_rows(c->p.Ly, sms);
+        KLMC_CUDA(configure_tiled());
+    }
+    const long long init[3] = {c->sweep, 0, (long long)(intptr_t)dev_trace};
+    KLMC_CUDA(cudaMemcpyAsync(c->state + kSweepBase, init, sizeof(init), cudaMemcpyHostToDevice,
+                              c->stream));
+    const int K = (trace_every > 0 && trace_every <= 64) ? (int)trace_every : 8;
+    cudaGraphExec_t exec = nullptr;
+    klmc_status st = tiled_graph(c, K, &exec);
+    if (st != KLMC_OK) return st;
+    int64_t done = 0;
+    while (done < n_mcs) {
+        const int64_t next = trace_every > 0 ? (done / trace_every + 1) * trace_every : n_mcs;
+        const int64_t upto = next < n_mcs ? next : n_mcs;
+        while (upto - done >= K) {
+            KLMC_CUDA(cudaGraphLaunch(exec, c->stream));
+            done += K;
+        }
+        if (upto > done) {
+            const int r = (int)(upto - done);
+            KLMC_CUDA(launch_tiled_phases(c->job, c->tiled_H, 0, r, c->stream));
+            KLMC_CUDA(launch_advance(c->state, r, c->stream));
+            done = upto;
+        }
+        if (trace_every > 0 && done % trace_every == 0) KLMC_CUDA(launch_trace(c->state, c->stream));
+    }
+    c->sweep += n_mcs;
+    return KLMC_OK;
+}
+
 klmc_status sweep_one(klmc_ctx *c, int64_t n_mcs, int64_t trace_every, int64_t *dev_trace)
 {
     if (!c) return fail(KLMC_EINVAL, "ctx is NULL");
@@ -287,6 +363,7 @@ klmc_status sweep_one(klmc_ctx *c, int64_t n_mcs, int64_t trace_every, int64_t *
     if (trace_every < 0 || (trace_every > 0 && !dev_trace))
         return fail(KLMC_EINVAL, "trace_every > 0 needs a device trace buffer");
     if (n_mcs == 0) return KLMC_OK;
+    if (c->cluster < 0) return sweep_tiled(c, n_mcs, trace_every, dev_trace);
     klmc_status st = check_resident(c, c->cluster);
     if (st != KLMC_OK) return st;
     if (trace_every > 0 && n_mcs / trace_every > 0)
@@ -539,6 +616,8 @@ klmc_status klmc_batch_create(klmc_batch **out, const klmc_params *reps, int32_t
         p.stream = reps[0].stream;
         klmc_ctx *c = nullptr;
         klmc_status st = create_one(&c, &p, b);
+        if (st == KLMC_OK && c->cluster < 0)
+            st = fail(KLMC_EINVAL, "lattice too large for a batched resident launch");
         if (st == KLMC_OK) st = check_resident(c, c->cluster);
         if (st != KLMC_OK) {
             std::string msg = "replica " + std::to_string(i) + ": " + g_err;

@@ -21,7 +21,10 @@ enum StateSlot : int {
     kAccepts = 4,
     kScratch0 = 5,  // recount result
     kNA = 6,        // A-site count after a device-side lattice load
-    kStateSlots = 8
+    kSweepBase = 7, // absolute sweep index read by the tiled phase kernels
+    kTracePos = 8,  // next entry of the energy trace (tiled path)
+    kTracePtr = 9,  // device address of the energy trace (tiled path)
+    kStateSlots = 12
 };
 
 // Static description of one lattice for the sweep kernels.
@@ -63,6 +66,15 @@ cudaError_t launch_resident_sweep(const SweepJob *d_jobs, const SweepCall *d_cal
 // Single lattice: job and call passed by value as kernel parameters.
 cudaError_t launch_resident_sweep_one(const SweepJob &job, const SweepCall &call, int cluster,
                                       size_t smem_bytes, cudaStream_t stream);
+
+// Tiled path for lattices too large for shared memory: one launch per phase,
+// CTAs of H-row bands (tiled_band_rows), sweep index read from state[kSweepBase].
+cudaError_t configure_tiled();
+int tiled_band_rows(int Ly, int sm_count);
+size_t tiled_smem_bytes(int Lx, int H);
+cudaError_t launch_tiled_phases(const SweepJob &job, int H, int k0, int n_sweeps, cudaStream_t stream);
+cudaError_t launch_advance(long long *state, int n, cudaStream_t stream);
+cudaError_t launch_trace(long long *state, cudaStream_t stream);
 
 // Initial placement: the nA sites with the smallest (64-bit Philox key, index).
 cudaError_t launch_init_lattice(void *lat, int packing, int Lx, int Ly, int pitch, uint32_t key0,

@@ -36,195 +36,7 @@
 namespace klmc {
 namespace {
 
-struct PhaseP {
-    int oi, rx, ry, px, py, umax;
-    int a1, n1, a2, n2, M1;  // this band's anchor rows: m in [a1, a1+n1) u [a2, a2+n2)
-    int ntask;
-};
-
-// Philox4x32-10 (Salmon et al., SC'11): ten rounds of two 32x32->64 products,
-// the high halves mixed into the other words with the round key; Weyl key bump.
-struct Philox4 {
-    uint32_t v[4];
-};
-
-__device__ __forceinline__ Philox4 philox4(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
-                                           uint32_t k0, uint32_t k1)
-{
-#pragma unroll
-    for (int r = 0; r < 10; ++r) {
-        unsigned long long p0 = (unsigned long long)c0 * 0xD2511F53ull;
-        unsigned long long p1 = (unsigned long long)c2 * 0xCD9E8D57ull;
-        uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0;
-        uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1;
-        c1 = (uint32_t)p1;
-        c3 = (uint32_t)p0;
-        c0 = n0;
-        c2 = n2;
-        k0 += 0x9E3779B9u;
-        k1 += 0xBB67AE85u;
-    }
-    Philox4 out;
-    out.v[0] = c0; out.v[1] = c1; out.v[2] = c2; out.v[3] = c3;
-    return out;
-}
-
-// Word 0 of Philox4x32-10 for two counters that differ only in word 0, computed
-// in lockstep so the two dependency chains overlap.
-__device__ __forceinline__ void philox2_w0(uint32_t a0, uint32_t b0, uint32_t c1, uint32_t c2,
-                                           uint32_t c3, uint32_t k0, uint32_t k1, uint32_t &ra,
-                                           uint32_t &rb)
-{
-    uint32_t a1 = c1, a2 = c2, a3 = c3, b1 = c1, b2 = c2, b3 = c3;
-#pragma unroll
-    for (int r = 0; r < 10; ++r) {
-        const unsigned long long pa0 = (unsigned long long)a0 * 0xD2511F53ull;
-        const unsigned long long pa1 = (unsigned long long)a2 * 0xCD9E8D57ull;
-        const unsigned long long pb0 = (unsigned long long)b0 * 0xD2511F53ull;
-        const unsigned long long pb1 = (unsigned long long)b2 * 0xCD9E8D57ull;
-        const uint32_t na0 = (uint32_t)(pa1 >> 32) ^ a1 ^ k0;
-        const uint32_t na2 = (uint32_t)(pa0 >> 32) ^ a3 ^ k1;
-        const uint32_t nb0 = (uint32_t)(pb1 >> 32) ^ b1 ^ k0;
-        const uint32_t nb2 = (uint32_t)(pb0 >> 32) ^ b3 ^ k1;
-        a1 = (uint32_t)pa1; a3 = (uint32_t)pa0; a0 = na0; a2 = na2;
-        b1 = (uint32_t)pb1; b3 = (uint32_t)pb0; b0 = nb0; b2 = nb2;
-        k0 += 0x9E3779B9u;
-        k1 += 0xBB67AE85u;
-    }
-    ra = a0;
-    rb = b0;
-}
-
-__device__ __forceinline__ int floor_div(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
-__device__ __forceinline__ int ceil_div(int a, int b) { return -floor_div(-a, b); }
-
-// Phase parameters of (sweep s, phase f) and this band's share of its anchor rows.
-// Orientation 1 is (0,1) in both geometries.
-__device__ void phase_params(int geometry, int Lx, int Ly, int W, int Y0, int Y1, uint32_t k0,
-                             uint32_t k1, long long s, int f, PhaseP *P)
-{
-    Philox4 w = philox4(0xFFFFFFFFu, (uint32_t)f, (uint32_t)(unsigned long long)s,
-                        (uint32_t)((unsigned long long)s >> 32), k0, k1);
-    const int nO = geometry == kTRI6 ? 3 : 2;
-    const int oi = (int)__umulhi(w.v[0], (uint32_t)nO);
-    const int rx = (int)__umulhi(w.v[1], (uint32_t)Lx);
-    const int ry = (int)__umulhi(w.v[2], (uint32_t)Ly);
-    int px, py, Kx, My;
-    if (oi == 1) {
-        px = 2; py = 4;
-        Kx = (Lx - 2) / 2 + 1;
-        My = (Ly - 3) / 4 + 1;
-    } else {
-        px = 4; py = 2;
-        Kx = (Lx - 3) / 4 + 1;
-        My = (Ly - 2) / 2 + 1;
-    }
-    // Anchor rows y_m = (ry + py m) mod Ly, m < My: unwrapped for m < M1.
-    const int M1 = min(My, ceil_div(Ly - ry, py));
-    const int a1 = max(ceil_div(Y0 - ry, py), 0);
-    const int b1 = min(floor_div(Y1 - 1 - ry, py), M1 - 1);
-    const int a2 = max(ceil_div(Y0 + Ly - ry, py), M1);
-    const int b2 = min(floor_div(Y1 - 1 + Ly - ry, py), My - 1);
-    P->oi = oi; P->rx = rx; P->ry = ry; P->px = px; P->py = py;
-    P->umax = px * (Kx - 1);
-    P->a1 = a1; P->n1 = max(0, b1 - a1 + 1);
-    P->a2 = a2; P->n2 = max(0, b2 - a2 + 1);
-    P->M1 = M1;
-    P->ntask = (P->n1 + P->n2) * W;
-}
-
-// Bits p of the word at x0 with x0 + p in [lo, hi].
-__device__ __forceinline__ uint32_t range_mask(int lo, int hi, int x0)
-{
-    int a = max(lo - x0, 0), b = min(hi - x0, 31);
-    if (a > b) return 0u;
-    return (0xFFFFFFFFu >> (31 - b)) & (0xFFFFFFFFu << a);
-}
-
-// Anchors of the phase in the word at x0: x = (rx + px k) mod Lx, k < Kx.
-__device__ __forceinline__ uint32_t anchor_mask(int x0, const PhaseP &P, int Lx)
-{
-    const uint32_t rep = P.px == 4 ? 0x11111111u : 0x55555555u;
-    const int pm = P.px - 1;
-    const int hi1 = min(P.rx + P.umax, Lx - 1);
-    if (x0 >= P.rx && x0 + 31 <= hi1) return rep << ((P.rx - x0) & pm);  // whole word in range
-    uint32_t m = (rep << ((P.rx - x0) & pm)) & range_mask(P.rx, hi1, x0);
-    const int hi2 = min(P.rx - 1, P.rx + P.umax - Lx);  // wrapped part of the anchor row
-    if (hi2 >= 0) m |= (rep << ((P.rx - Lx - x0) & pm)) & range_mask(0, hi2, x0);
-    return m;
-}
-
-__device__ __forceinline__ uint32_t fsr(uint32_t lo, uint32_t hi, int s)
-{
-    return __funnelshift_r(lo, hi, s);
-}
-
-// Full adder on bit planes.
-__device__ __forceinline__ void fa(uint32_t a, uint32_t b, uint32_t c, uint32_t &s, uint32_t &cy)
-{
-    s = a ^ b ^ c;
-    cy = (a & b) | (c & (a ^ b));
-}
-
-struct Planes {
-    uint32_t s0, s1, s2, s3;
-};
-
-// Bit-sliced sum of ten 1-bit inputs (0..10).
-__device__ __forceinline__ Planes count10(uint32_t e0, uint32_t e1, uint32_t e2, uint32_t e3,
-                                          uint32_t e4, uint32_t e5, uint32_t e6, uint32_t e7,
-                                          uint32_t e8, uint32_t e9)
-{
-    uint32_t sa, ca, sb, cb, sc, cc, sd, cd;
-    fa(e0, e1, e2, sa, ca);
-    fa(e3, e4, e5, sb, cb);
-    fa(e6, e7, e8, sc, cc);
-    fa(sa, sb, sc, sd, cd);             // weight-1: sd; weight-2: cd
-    Planes P;
-    P.s0 = sd ^ e9;
-    uint32_t ce = sd & e9;              // weight 2
-    uint32_t s2a, c2a, s2b, c2b;
-    fa(ca, cb, cc, s2a, c2a);           // weight 2 -> s2a (w2), c2a (w4)
-    fa(cd, ce, s2a, s2b, c2b);          // weight 2 -> s2b (w2), c2b (w4)
-    P.s1 = s2b;
-    P.s2 = c2a ^ c2b;
-    P.s3 = c2a & c2b;
-    return P;
-}
-
-// Bit-sliced sum of six 1-bit inputs (0..6).
-__device__ __forceinline__ Planes count6(uint32_t e0, uint32_t e1, uint32_t e2, uint32_t e3,
-                                         uint32_t e4, uint32_t e5)
-{
-    uint32_t sa, ca, sb, cb, s2, c2;
-    fa(e0, e1, e2, sa, ca);
-    fa(e3, e4, e5, sb, cb);
-    Planes P;
-    P.s0 = sa ^ sb;
-    fa(ca, cb, sa & sb, s2, c2);
-    P.s1 = s2;
-    P.s2 = c2;
-    P.s3 = 0u;
-    return P;
-}
-
-__device__ __forceinline__ uint32_t eqm(uint32_t v, uint32_t t) { return ~(v ^ t); }
-
-// Positions that need a draw: the exchange raises the energy when omega > 0
-// (sign > 0: S > z - 1) or lowers it when omega < 0 (sign < 0: S < z - 1).
-template <int G>
-__device__ __forceinline__ uint32_t draw_positions(const Planes &S, int sign)
-{
-    uint32_t up, down;
-    if (G == kTRI6) {  // z - 1 = 5, S in 0..10
-        up = S.s3 | (S.s2 & S.s1);                     // S >= 6
-        down = ~(S.s3 | (S.s2 & (S.s1 | S.s0)));       // S <= 4
-    } else {           // z - 1 = 3, S in 0..6
-        up = S.s2;                                     // S >= 4
-        down = ~(S.s2 | (S.s1 & S.s0));                // S <= 2
-    }
-    return sign > 0 ? up : (sign < 0 ? down : 0u);
-}
+#include "sweep_common.cuh"
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p)
 {
@@ -351,85 +163,14 @@ __device__ __forceinline__ void run_phase(const uint32_t *lat, const Geo &g, con
             if (y >= g.Ly) y -= g.Ly;
             x0 = j << 5;
             am = anchor_mask(x0, P, g.Lx);
-            const uint32_t *r0 = lat + (size_t)(y - g.Y0 + 2) * g.RW;
-            const uint32_t *rm = r0 - g.RW, *rp = r0 + g.RW;
-            const uint32_t a0 = r0[j], a1 = r0[j + 1], a2 = r0[j + 2];
-            const uint32_t Am = fsr(a0, a1, 31), A0 = a1, A1 = fsr(a1, a2, 1);
-            if (G == kTRI6 && OI == 0) {
-                const uint32_t m1 = rm[j + 1], m2 = rm[j + 2];
-                const uint32_t p0 = rp[j], p1 = rp[j + 1], p2 = rp[j + 2];
-                const uint32_t M0 = m1, M1 = fsr(m1, m2, 1), M2 = fsr(m1, m2, 2);
-                const uint32_t A2 = fsr(a1, a2, 2);
-                const uint32_t Pm = fsr(p0, p1, 31), P0 = p1, P1 = fsr(p1, p2, 1);
-                ta = A0; tb = A1;
-                S = count10(eqm(Am, ta), eqm(P0, ta), eqm(M0, ta), eqm(M1, ta), eqm(Pm, ta),
-                            eqm(A2, tb), eqm(P1, tb), eqm(M1, tb), eqm(M2, tb), eqm(P0, tb));
-            } else if (G == kTRI6 && OI == 1) {
-                const uint32_t *rq = rp + g.RW;
-                const uint32_t m1 = rm[j + 1], m2 = rm[j + 2];
-                const uint32_t p0 = rp[j], p1 = rp[j + 1], p2 = rp[j + 2];
-                const uint32_t q0 = rq[j], q1 = rq[j + 1];
-                const uint32_t M0 = m1, M1 = fsr(m1, m2, 1);
-                const uint32_t Pm = fsr(p0, p1, 31), P0 = p1, P1 = fsr(p1, p2, 1);
-                const uint32_t Qm = fsr(q0, q1, 31), Q0 = q1;
-                ta = A0; tb = P0;
-                S = count10(eqm(A1, ta), eqm(Am, ta), eqm(M0, ta), eqm(M1, ta), eqm(Pm, ta),
-                            eqm(P1, tb), eqm(Pm, tb), eqm(Q0, tb), eqm(A1, tb), eqm(Qm, tb));
-            } else if (G == kTRI6 && OI == 2) {
-                const uint32_t *rn = rm - g.RW;
-                const uint32_t n1 = rn[j + 1], n2 = rn[j + 2];
-                const uint32_t m1 = rm[j + 1], m2 = rm[j + 2];
-                const uint32_t p0 = rp[j], p1 = rp[j + 1];
-                const uint32_t N1 = fsr(n1, n2, 1), N2 = fsr(n1, n2, 2);
-                const uint32_t M0 = m1, M1 = fsr(m1, m2, 1), M2 = fsr(m1, m2, 2);
-                const uint32_t Pm = fsr(p0, p1, 31), P0 = p1;
-                ta = A0; tb = M1;
-                S = count10(eqm(A1, ta), eqm(Am, ta), eqm(P0, ta), eqm(M0, ta), eqm(Pm, ta),
-                            eqm(M2, tb), eqm(M0, tb), eqm(A1, tb), eqm(N1, tb), eqm(N2, tb));
-            } else if (G == kSQ4 && OI == 0) {
-                const uint32_t m1 = rm[j + 1], m2 = rm[j + 2];
-                const uint32_t p1 = rp[j + 1], p2 = rp[j + 2];
-                const uint32_t M0 = m1, M1 = fsr(m1, m2, 1);
-                const uint32_t A2 = fsr(a1, a2, 2);
-                const uint32_t P0 = p1, P1 = fsr(p1, p2, 1);
-                ta = A0; tb = A1;
-                S = count6(eqm(Am, ta), eqm(P0, ta), eqm(M0, ta), eqm(A2, tb), eqm(P1, tb),
-                           eqm(M1, tb));
-            } else {  // SQ4, (0,1)
-                const uint32_t *rq = rp + g.RW;
-                const uint32_t m1 = rm[j + 1];
-                const uint32_t p0 = rp[j], p1 = rp[j + 1], p2 = rp[j + 2];
-                const uint32_t q1 = rq[j + 1];
-                const uint32_t M0 = m1;
-                const uint32_t Pm = fsr(p0, p1, 31), P0 = p1, P1 = fsr(p1, p2, 1);
-                const uint32_t Q0 = q1;
-                ta = A0; tb = P0;
-                S = count6(eqm(A1, ta), eqm(Am, ta), eqm(M0, ta), eqm(P1, tb), eqm(Pm, tb),
-                           eqm(Q0, tb));
-            }
+            evaluate<G, OI>(lat + (size_t)(y - g.Y0 + 2) * g.RW, g.RW, j, ta, tb, S);
         }
         const uint32_t unl = (ta ^ tb) & am;
         const uint32_t dmask = unl & draw_positions<G>(S, g.sign);
         uint32_t acc = unl & ~dmask;
 
-        // Each lane draws for its own anchors, two Philox evaluations at a time.
-        const uint32_t site_base = (uint32_t)(y * g.Lx + x0);
-        uint32_t dm = dmask;
-        while (dm != 0u) {
-            const int p1 = __ffs(dm) - 1;
-            dm &= dm - 1u;
-            const int p2 = dm != 0u ? __ffs(dm) - 1 : p1;  // an odd last draw is repeated
-            dm &= dm - 1u;
-            uint32_t r1, r2;
-            philox2_w0(site_base + (uint32_t)p1, site_base + (uint32_t)p2, (uint32_t)f, s_lo, s_hi,
-                       g.k0, g.k1, r1, r2);
-            const uint32_t S1 = ((S.s0 >> p1) & 1u) | (((S.s1 >> p1) & 1u) << 1) |
-                                (((S.s2 >> p1) & 1u) << 2) | (((S.s3 >> p1) & 1u) << 3);
-            const uint32_t S2 = ((S.s0 >> p2) & 1u) | (((S.s1 >> p2) & 1u) << 1) |
-                                (((S.s2 >> p2) & 1u) << 2) | (((S.s3 >> p2) & 1u) << 3);
-            if ((uint64_t)r1 < thr[S1]) acc |= 1u << p1;
-            if ((uint64_t)r2 < thr[S2]) acc |= 1u << p2;
-        }
+        acc |= draw_accepts(dmask, S, (uint32_t)(y * g.Lx + x0), (uint32_t)f, s_lo, s_hi, g.k0,
+                            g.k1, thr);
         const int nd = __popc(dmask);
 
         A.att += __popc(am);
@@ -461,15 +202,6 @@ __device__ __forceinline__ void run_phase(const uint32_t *lat, const Geo &g, con
             if (wrap0) flip_global_row(g, y + bdy, 0, 1ull);
         }
     }
-}
-
-__device__ __forceinline__ uint32_t load_site(const SweepJob &J, int x, int y)
-{
-    if (J.packing == kPackBit) {
-        const uint32_t *row = (const uint32_t *)J.lat + (size_t)y * J.pitch;
-        return (row[x >> 5] >> (x & 31)) & 1u;
-    }
-    return ((const uint8_t *)J.lat)[(size_t)y * J.pitch + x] ? 1u : 0u;
 }
 
 template <typename T>
@@ -539,18 +271,7 @@ resident_sweep_kernel(const SweepJob *__restrict__ jobs, const SweepCall *__rest
         int y = g.Y0 - 2 + lr;
         y %= g.Ly;
         if (y < 0) y += g.Ly;
-        const int pos0 = 32 * w - 32;
-        uint32_t v = 0u;
-        if (J.packing == kPackBit && pos0 >= 0 && pos0 + 32 <= g.Lx) {
-            v = ((const uint32_t *)J.lat)[(size_t)y * J.pitch + (w - 1)];
-        } else {
-            for (int b = 0; b < 32; ++b) {
-                int x = (pos0 + b) % g.Lx;
-                if (x < 0) x += g.Lx;
-                v |= load_site(J, x, y) << b;
-            }
-        }
-        lat[idx] = v;
+        lat[idx] = padded_word(J.lat, J.packing, J.pitch, y, w, g.Lx, g.W);
     }
     if (tid < 16) thr[tid] = J.thr[tid];
     if (tid < 8)

@@ -87,12 +87,69 @@ def test_cluster_size_parity(geometry, cluster, Lx, Ly, nA, bw):
     assert tr.cpu().numpy().tolist() == ref.trace.tolist()
 
 
+@pytest.mark.parametrize("geometry", GEOMS)
+@pytest.mark.parametrize("packing", PACKS)
+@pytest.mark.parametrize("Lx,Ly,nA,bw,n_mcs,trace_every", [
+    (4, 4, 8, 0.6, 9, 3), (5, 7, 17, 1.0, 11, 0), (64, 64, 2048, 0.6, 21, 10), (33, 95, 1500, -0.4, 17, 5),
+    (100, 101, 3030, 0.85, 12, 4), (257, 66, 5000, 0.0, 9, 0),
+])
+def test_tiled_path_parity(geometry, packing, Lx, Ly, nA, bw, n_mcs, trace_every):
+    """The per-phase tiled path (graph replays of K sweeps plus direct launches for
+    the rest) gives the same trajectory as the oracle."""
+    seed = 5 + Lx + Ly
+    lat = make(Lx, Ly, nA, bw, seed, geometry, packing, cluster=-1)
+    assert lat.launch_shape()[0] == -1
+    ref = oracle.run(Lx, Ly, geometry, bw, seed, oracle.init(Lx, Ly, nA, seed), 0, n_mcs,
+                     trace_every=trace_every)
+    if trace_every:
+        tr = lat.sweep_traced(n_mcs, trace_every)
+        torch.cuda.synchronize()
+        assert tr.cpu().numpy().tolist() == ref.trace.tolist()
+    else:
+        lat.sweep(n_mcs)
+    assert_same_run(lat, ref)
+
+
+def test_tiled_split_equals_whole():
+    Lx, Ly, nA, bw, seed = 90, 70, 2000, 0.7, 44
+    a = make(Lx, Ly, nA, bw, seed, cluster=-1)
+    for n in (3, 8, 1, 16, 5):
+        a.sweep(n)
+    ref = oracle.run(Lx, Ly, klmc.TRI6, bw, seed, oracle.init(Lx, Ly, nA, seed), 0, 33)
+    assert_same_run(a, ref)
+
+
+def test_8192_lattice_tiled():
+    """The 8192 x 8192, 1 bit per site, omega/kT = 0.85 lattice: too large for
+    shared memory, so it runs on the tiled path.  One sweep against the oracle;
+    then 25 more traced sweeps checked by invariants."""
+    L = 8192
+    nA = L * L // 2
+    lat = make(L, L, nA, 0.85, 7)
+    assert lat.launch_shape()[0] == -1
+    t0 = lat.get_lattice()
+    assert np.array_equal(t0, oracle.init(L, L, nA, 7))
+    lat.sweep(1)
+    ref = oracle.run(L, L, klmc.TRI6, 0.85, 7, t0, 0, 1)
+    assert_same_run(lat, ref)
+    tr = lat.sweep_traced(25, 10)
+    torch.cuda.synchronize()
+    t = lat.get_lattice()
+    assert int(t.sum()) == nA
+    n_end = lat.energy()[0]
+    assert n_end == lat.energy_recount()
+    assert tr.cpu().numpy().tolist()[-1] <= ref.n_unlike  # demixing lowers the energy
+    assert lat.counters()["sweeps"] == 26
+
+
 def test_cluster_size_rejected():
     with pytest.raises(klmc.KlmcError) as e:
         make(16, 16, 100, 0.5, 1, cluster=8)  # bands of 2 rows
     assert e.value.status == 1
     with pytest.raises(klmc.KlmcError):
         make(64, 64, 100, 0.5, 1, cluster=17)
+    with pytest.raises(klmc.KlmcError):
+        make(64, 64, 100, 0.5, 1, cluster=-2)
 
 
 @pytest.mark.parametrize("geometry", GEOMS)
@@ -252,11 +309,14 @@ def test_large_lattice_on_full_cluster():
     Lx = Ly = 2048
     nA = Lx * Ly * 3 // 10
     lat = make(Lx, Ly, nA, 0.7, 9)
+    assert lat.launch_shape()[0] == 16
     lat.sweep(1)
     ref = oracle.run(Lx, Ly, klmc.TRI6, 0.7, 9, oracle.init(Lx, Ly, nA, 9), 0, 1)
     assert_same_run(lat, ref)
+    # too large for a 16-CTA cluster: the automatic choice falls back to the tiled path
+    assert make(6000, 6000, 1000, 0.5, 1).launch_shape()[0] == -1
     with pytest.raises(klmc.KlmcError) as e:
-        make(6000, 6000, 1000, 0.5, 1).sweep(1)
+        make(6000, 6000, 1000, 0.5, 1, cluster=16).sweep(1)
     assert e.value.status == 1
 
 
