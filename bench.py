@@ -72,6 +72,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--mcs", type=int, default=N_MCS, help="steps per run (default: the workload's)")
+    ap.add_argument("--workload", choices=["c2", "c1", "c3", "c4"], default="c2",
+                    help="c2 (default): 400x400 x 5 omega; c1: 64x64; c3: 8192x8192; c4: 256 replicas")
     ap.add_argument("--skip-plain", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     return ap.parse_args()
@@ -202,6 +204,198 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# Other workloads (the default driver line is the 400x400 x 5 omega workload).
+# ---------------------------------------------------------------------------
+C1 = dict(L=64, n_A=2048, omega=0.6, seed=1, mcs=1000, hist_every=100)
+C3 = dict(L=8192, omega=0.85, seed=7, mcs=1000, trace_every=10)
+C4 = dict(n=256, L_min=100, L_max=1024, f_min=0.1, f_max=0.5, w_min=0.1, w_max=1.2, mcs=5000,
+          seed0=1000, draw_seed=20260)
+
+
+def c4_replicas():
+    """256 replicas: side log-uniform over [100, 1024], A fraction uniform over
+    [0.1, 0.5], omega/kT uniform over [0.1, 1.2], seed 1000 + r (drawn from a fixed
+    numpy generator so every run uses the same set)."""
+    import numpy as np
+
+    rng = np.random.default_rng(C4["draw_seed"])
+    out = []
+    for r in range(C4["n"]):
+        L = int(round(float(np.exp(rng.uniform(np.log(C4["L_min"]), np.log(C4["L_max"]))))))
+        out.append(dict(Lx=L, Ly=L, fraction_A=float(rng.uniform(C4["f_min"], C4["f_max"])),
+                        omega_over_kT=float(rng.uniform(C4["w_min"], C4["w_max"])),
+                        seed=C4["seed0"] + r))
+    return out
+
+
+def _time_steps(torch, stream, flush, step, K, W):
+    for _ in range(W):
+        step()
+    torch.cuda.synchronize()
+    evs = []
+    for _ in range(K):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step()
+        b.record(stream)
+        evs.append((a, b))
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in evs]
+
+
+def _roofline(kernel, launch_ms, attempts_launch, p_draw, sm_count, sm_mhz, ctas, extra=None):
+    ops_attempt = C_PAIR + p_draw * C_PHILOX
+    peak = sm_count * INT32_LANES_PER_SM * sm_mhz * 1e6 / 1e12
+    achieved = ops_attempt * attempts_launch / (launch_ms * 1e-3) / 1e12
+    d = {"bound": "alu", "kernel": kernel, "achieved": achieved, "peak": peak,
+         "unit": "Tops/s (INT32 lane-ops)", "frac": achieved / peak, "traffic": None,
+         "ops_per_attempt": ops_attempt, "p_draw": p_draw, "launch_ms": launch_ms,
+         "attempts_per_launch": attempts_launch, "ctas_per_launch": ctas,
+         "peak_basis": (f"{sm_count} SMs x {INT32_LANES_PER_SM} INT32 lanes/clk x median SM clock "
+                        f"{sm_mhz:.0f} MHz (derived; probes/int_peak.cu)")}
+    d.update(extra or {})
+    return d
+
+
+def bench_other(args, klmc, torch, np):
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    sm_count = torch.cuda.get_device_properties(local).multi_processor_count
+    clocks = ClockSampler(gpu_smi_id(torch, local))
+    line = {"metric": "Kawasaki exchange attempts/s", "unit": "attempts/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic"}
+    if args.workload == "c1":
+        c = C1
+        lat = klmc.Lattice(c["L"], c["L"], n_A=c["n_A"], omega_over_kT=c["omega"], seed=c["seed"],
+                           packing=klmc.PACK_BYTE)
+        lat.autotune(16)
+        init = torch.from_numpy(lat.get_lattice()).cuda()
+        nseg = c["mcs"] // c["hist_every"]
+        cap = int(np.sqrt(2.0 * lat.N)) + 2
+        sz = torch.zeros((nseg, cap), dtype=torch.int64, device="cuda")
+        ct = torch.zeros_like(sz)
+        nd = torch.zeros(nseg, dtype=torch.int64, device="cuda")
+        sweep_ev = []
+
+        def step(record=False):
+            lat.set_lattice_device(init, 0)
+            for k in range(nseg):
+                if record:
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                lat.sweep(c["hist_every"])
+                if record:
+                    e1.record(stream)
+                    sweep_ev.append((e0, e1))
+                lat.cluster_histogram_device(1, sz[k], ct[k], nd[k:k + 1])
+
+        clocks.start()
+        ms = _time_steps(torch, stream, flush, lambda: step(True), args.steps, args.warmup)
+        clk = clocks.stop()
+        cnt = lat.counters()
+        attempts = cnt["attempts"]
+        ms_step = sum(ms) / len(ms)
+        tail = sweep_ev[-nseg * args.steps:]
+        launch_ms = sum(a.elapsed_time(b) for a, b in tail) / len(tail)
+        C, T = lat.launch_shape()
+        line.update({"value": attempts / (ms_step * 1e-3), "ms_per_step": ms_step,
+                     "config": {"workload": "64x64 TRI6 periodic, 2048 A + 2048 B random start, "
+                                "omega/kT 0.6, int8 (1 byte/site) store, 1000 MCS, A-cluster "
+                                "histogram every 100 MCS", "form": "plain (one lattice)",
+                                "l2": "flushed between steps"},
+                     "us_per_mcs": ms_step * 1e3 / c["mcs"],
+                     "roofline": _roofline("resident_sweep_kernel", launch_ms,
+                                           attempts // nseg, cnt["draws"] / attempts, sm_count,
+                                           clk["sm_mhz"] if clk else 2070.0, C,
+                                           {"cluster": C, "threads_per_cta": T}),
+                     "clocks": clk, "gpu_launches": args.steps * (3 + nseg * (1 + LAUNCHES_HISTOGRAM))})
+    elif args.workload == "c3":
+        c = C3
+        line["variants"] = {}
+        for geom, name in ((klmc.TRI6, "TRI6"), (klmc.SQ4, "SQ4")):
+            L = c["L"]
+            lat = klmc.Lattice(L, L, n_A=L * L // 2, omega_over_kT=c["omega"], seed=c["seed"],
+                               geometry=geom)
+            init = torch.from_numpy(lat.get_lattice()).cuda()
+            trace = torch.zeros(c["mcs"] // c["trace_every"], dtype=torch.int64, device="cuda")
+
+            def step():
+                lat.set_lattice_device(init, 0)
+                lat.sweep_traced(c["mcs"], c["trace_every"], out=trace)
+
+            clocks.start()
+            ms = _time_steps(torch, stream, flush, step, args.steps, args.warmup)
+            clk = clocks.stop()
+            cnt = lat.counters()
+            ms_step = sum(ms) / len(ms)
+            attempts = cnt["attempts"]
+            launch_ms = ms_step / (8 * c["mcs"])  # per phase launch, graph gaps included
+            rl = _roofline("tiled_phase_kernel", launch_ms, attempts // (8 * c["mcs"]),
+                           cnt["draws"] / attempts, sm_count, clk["sm_mhz"] if clk else 2070.0,
+                           -1, {"note": "per-launch time = step time / phase launches (graph replays)"})
+            v = {"value": attempts / (ms_step * 1e-3), "ms_per_step": ms_step, "roofline": rl,
+                 "clocks": clk, "final_n_unlike": int(trace[-1].item())}
+            line["variants"][name] = v
+            if geom == klmc.TRI6:
+                line.update({"value": v["value"], "ms_per_step": ms_step, "roofline": rl, "clocks": clk})
+            lat.close()
+        line["config"] = {"workload": "8192x8192 periodic, 50/50 random start, 1 bit/site, omega/kT "
+                          "0.85, 1000 MCS, energy trace every 10 MCS (TRI6; SQ4 in variants)",
+                          "form": "tiled per-phase launches replayed from a CUDA graph of 10 MCS",
+                          "l2": "lattice (8 MiB) fits L2; flushed between steps"}
+        line["gpu_launches"] = args.steps * (3 + 8 * c["mcs"] + 2 * c["mcs"] // c["trace_every"])
+    elif args.workload == "c4":
+        reps = c4_replicas()
+        b = klmc.Batch([dict(r, packing=klmc.PACK_BIT) for r in reps])
+        inits = [torch.from_numpy(l.get_lattice()).cuda() for l in b.replicas]
+        groups = {}
+        for l in b.replicas:
+            C, _ = l.launch_shape()
+            groups[C] = groups.get(C, 0) + 1
+
+        def step():
+            for l, t in zip(b.replicas, inits):
+                l.set_lattice_device(t, 0)
+            b.sweep(C4["mcs"])
+
+        clocks.start()
+        ms = _time_steps(torch, stream, flush, step, args.steps, args.warmup)
+        clk = clocks.stop()
+        cnts = [l.counters() for l in b.replicas]
+        attempts = sum(x["attempts"] for x in cnts)
+        draws = sum(x["draws"] for x in cnts)
+        ms_step = sum(ms) / len(ms)
+        ctas = sum(C * n for C, n in groups.items())
+        line.update({"value": attempts / (ms_step * 1e-3), "ms_per_step": ms_step,
+                     "config": {"workload": "batched: 256 replicas, side log-uniform 100-1024, A "
+                                "fraction U[0.1,0.5], omega/kT U[0.1,1.2], seeds 1000+r, 5000 MCS each",
+                                "form": "batched: one launch per cluster-size group, groups on "
+                                        "concurrent streams", "groups": {str(k): v for k, v in groups.items()},
+                                "l2": "flushed between steps"},
+                     "roofline": _roofline("resident_sweep_kernel", ms_step, attempts, draws / attempts,
+                                           sm_count, clk["sm_mhz"] if clk else 2070.0, ctas,
+                                           {"note": "launch time = step time (group launches overlap)"}),
+                     "clocks": clk, "gpu_launches": args.steps * (3 * len(reps) + len(groups))})
+        if not args.skip_plain:
+            sub = list(range(0, len(reps), 16))  # 16 replicas, one launch each, in turn
+            def step_plain():
+                for i in sub:
+                    b.replicas[i].set_lattice_device(inits[i], 0)
+                    b.replicas[i].sweep(C4["mcs"])
+            msp = _time_steps(torch, stream, flush, step_plain, 1, 1)
+            att_sub = sum(b.replicas[i].counters()["attempts"] for i in sub)
+            line["forms"] = {"batched": {"value": line["value"]},
+                             "plain": {"value": att_sub / (msp[0] * 1e-3),
+                                       "sample": f"{len(sub)} of the 256 replicas, one launch each"}}
+        b.close()
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     rank, world, local = dist_info()
@@ -228,6 +422,10 @@ def main():
             dist.barrier()
 
     klmc.build()
+    if args.workload != "c2":
+        if rank == 0:
+            bench_other(args, klmc, torch, np)
+        return
     n_mcs = args.mcs
     n_seg = n_mcs // HIST_EVERY
     assert n_seg * HIST_EVERY == n_mcs
@@ -238,6 +436,11 @@ def main():
     N = L * L
     stream = torch.cuda.current_stream()
 
+    # Tune the launch shape of this lattice size once (cached for the replicas).
+    probe = klmc.Lattice(L, L, fraction_A=FRACTION_A, omega_over_kT=OMEGAS[2], seed=99,
+                         packing=klmc.PACK_BIT)
+    tuned = probe.autotune(64)
+    probe.close()
     batch = klmc.Batch(reps)
     init_host = [batch.replicas[i].get_lattice() for i in range(nrun)]
     init_dev = [torch.from_numpy(t).cuda() for t in init_host]
@@ -403,7 +606,7 @@ def main():
         "config": {"workload": WORKLOAD,
                    "form": "batched (one resident launch, one thread-block cluster per lattice)",
                    "L": L, "runs": nrun, "mcs": n_mcs, "hist_every": HIST_EVERY,
-                   "parallelism": f"replicas x{world}",
+                   "parallelism": f"replicas x{world}", "tuned_shape": list(tuned),
                    "l2": "flushed between steps (256 MiB write outside the timed events)"},
         "sites_per_s": value,  # one attempt per site per MCS: sites x MCS / s
         "forms": forms,

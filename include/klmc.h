@@ -188,8 +188,20 @@ klmc_status klmc_set_lattice_device(klmc_ctx *c, const uint8_t *dev_in, int64_t 
  * Synchronises when n_A was last set on the device. */
 klmc_status klmc_get_shape(klmc_ctx *c, int32_t *Lx, int32_t *Ly, int32_t *geometry, int64_t *n_A);
 
-/* Launch shape of the handle's resident sweep: CTAs per lattice (thread-block
- * cluster size) and threads per CTA.  Either pointer may be NULL. */
+/* Autotuner: picks the fastest launch shape for this lattice's size by timing
+ * every valid shape -- 1, 2, 4, 8 or 16 CTAs per lattice with 512 (one CTA only)
+ * or 256 threads per CTA, and the tiled per-phase path -- for probe_sweeps sweeps
+ * on a scratch copy of the lattice at its current sweep index.  Every candidate's
+ * resulting lattice and counters must equal the first candidate's (exactness
+ * gate; a differing shape is an error, KLMC_ESTATE).  The choice is cached per
+ * (Lx, Ly, geometry, packing) for the process and applied to the handle; the
+ * lattice, counters and trajectory are unchanged.  Synchronises.  Either output
+ * pointer may be NULL.  ESTATE for a replica view. */
+klmc_status klmc_autotune(klmc_ctx *c, int32_t probe_sweeps, int32_t *cluster, int32_t *threads);
+
+/* Launch shape of the handle's sweep: CTAs per lattice (thread-block cluster
+ * size, -1 for the tiled per-phase path) and threads per CTA.  Either pointer may
+ * be NULL. */
 klmc_status klmc_get_launch(klmc_ctx *c, int32_t *cluster, int32_t *threads_per_cta);
 
 /* Waits for all work enqueued on the handle's stream. */
@@ -200,9 +212,12 @@ klmc_status klmc_synchronize(klmc_ctx *c);
 klmc_status klmc_destroy(klmc_ctx *c);
 
 /* Batched form: n independent replicas (own sizes, compositions, omega, seeds)
- * advanced together by one launch of the resident kernel, one thread-block
- * cluster per replica (the smallest cluster size any replica asks for).  All
- * replicas use the stream of reps[0]. */
+ * advanced together by the resident kernel, one thread-block cluster per replica
+ * (each replica's own cluster size, params.cluster or automatic).  Replicas that
+ * share a cluster size form one launch, larger lattices first; the launches of
+ * different sizes run on internal streams forked from and joined back to the
+ * stream of reps[0], which every replica uses.  Every replica must fit the
+ * shared-memory resident sweep. */
 klmc_status klmc_batch_create(klmc_batch **out, const klmc_params *reps, int32_t n);
 
 /* Enqueues n_mcs[i] steps for replica i (entries may differ; 0 skips). */

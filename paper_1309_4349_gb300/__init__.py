@@ -89,6 +89,7 @@ def lib():
         "klmc_set_lattice_device": [vp, vp, i64, i64],
         "klmc_get_shape": [vp, P(i32), P(i32), P(i32), P(i64)],
         "klmc_get_launch": [vp, P(i32), P(i32)],
+        "klmc_autotune": [vp, i32, P(i32), P(i32)],
         "klmc_synchronize": [vp],
         "klmc_destroy": [vp],
         "klmc_batch_create": [P(vp), P(Params), i32],
@@ -264,6 +265,13 @@ class Lattice:
         """Loads the lattice from a uint8 CUDA tensor of Lx*Ly entries (0/1), async."""
         assert t.is_cuda and t.dtype.itemsize == 1 and t.numel() == self.N and t.is_contiguous()
         _check(lib().klmc_set_lattice_device(self._h, t.data_ptr(), self.N, int(sweep_index)))
+
+    def autotune(self, probe_sweeps: int = 8):
+        """Times the valid launch shapes on a scratch copy and keeps the fastest
+        (all candidates must give identical results); returns (cluster, threads)."""
+        c, t = ctypes.c_int32(), ctypes.c_int32()
+        _check(lib().klmc_autotune(self._h, int(probe_sweeps), ctypes.byref(c), ctypes.byref(t)))
+        return c.value, t.value
 
     def launch_shape(self):
         """(CTAs per lattice, threads per CTA) of the resident sweep."""

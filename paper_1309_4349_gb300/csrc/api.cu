@@ -3,7 +3,9 @@
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
 #include <map>
+#include <mutex>
 #include <new>
 #include <string>
 #include <utility>
@@ -63,7 +65,8 @@ struct klmc_ctx {
     long long N = 0, nA = 0;
     bool nA_on_device = false;    // nA must be read back from state[kNA]
     int W = 0, pitch = 0;
-    int cluster = 1;              // CTAs per lattice in the resident sweep
+    int cluster = 1;              // CTAs per lattice in the resident sweep (-1: tiled path)
+    int threads = 512;            // threads per CTA of the resident sweep (512 or 256)
     size_t lat_bytes = 0;
     void *lat = nullptr;
     long long *state = nullptr;   // StateSlot array
@@ -88,9 +91,20 @@ struct klmc_batch {
     std::vector<klmc_ctx *> reps;
     SweepJob *djobs = nullptr;
     SweepCall *dcalls = nullptr;
+    int *dmap = nullptr;            // replica indices grouped by cluster size, largest first
     std::vector<SweepCall> hcalls;
     cudaStream_t stream = nullptr;
     klmc_ctx *mem_owner = nullptr;  // holds the batch arrays' allocations
+    // groups of replicas sharing a cluster size: (cluster, offset into dmap, count)
+    struct Group {
+        int cluster, threads, offset, count;
+        size_t smem;
+        cudaStream_t stream;
+        cudaEvent_t done;
+    };
+    std::vector<Group> groups;
+    std::vector<int> hmap;
+    cudaEvent_t fork = nullptr;
 };
 
 namespace {
@@ -211,6 +225,8 @@ klmc_status ensure_clusters(klmc_ctx *c)
     return KLMC_OK;
 }
 
+bool tuned_shape(int Lx, int Ly, int geometry, int packing, int *cluster, int *threads);
+
 klmc_status create_one(klmc_ctx **out, const klmc_params *p, klmc_batch *owner)
 {
     klmc_status st = validate(p);
@@ -230,6 +246,8 @@ klmc_status create_one(klmc_ctx **out, const klmc_params *p, klmc_batch *owner)
     if (p->cluster == 0 &&
         resident_smem_bytes(p->Lx, p->Ly, c->cluster) > (size_t)resident_max_smem_bytes())
         c->cluster = -1;  // automatic choice, too large for shared memory: tiled path
+    c->threads = resident_default_threads(c->cluster);
+    if (p->cluster == 0) tuned_shape(p->Lx, p->Ly, p->geometry, c->p.packing, &c->cluster, &c->threads);
     if (c->p.packing == KLMC_PACK_BIT) {
         c->pitch = (c->W + 3) / 4 * 4;  // 16-byte rows
         c->lat_bytes = (size_t)c->pitch * 4 * p->Ly;
@@ -374,10 +392,145 @@ klmc_status sweep_one(klmc_ctx *c, int64_t n_mcs, int64_t trace_every, int64_t *
     call.n_mcs = n_mcs;
     call.trace = (long long *)dev_trace;
     call.trace_every = trace_every;
-    KLMC_CUDA(launch_resident_sweep_one(c->job, call, c->cluster,
+    KLMC_CUDA(launch_resident_sweep_one(c->job, call, c->cluster, c->threads,
                                         resident_smem_bytes(c->p.Lx, c->p.Ly, c->cluster),
                                         c->stream));
     c->sweep += n_mcs;
+    return KLMC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner: launch shape per lattice size, chosen by timing on a scratch copy,
+// with every candidate's result required to be identical.
+// ---------------------------------------------------------------------------
+struct TuneKey {
+    int Lx, Ly, geometry, packing;
+    bool operator<(const TuneKey &o) const
+    {
+        if (Lx != o.Lx) return Lx < o.Lx;
+        if (Ly != o.Ly) return Ly < o.Ly;
+        if (geometry != o.geometry) return geometry < o.geometry;
+        return packing < o.packing;
+    }
+};
+std::mutex g_tune_mutex;
+std::map<TuneKey, std::pair<int, int>> g_tune_cache;
+
+bool tuned_shape(int Lx, int Ly, int geometry, int packing, int *cluster, int *threads)
+{
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    auto it = g_tune_cache.find(TuneKey{Lx, Ly, geometry, packing});
+    if (it == g_tune_cache.end()) return false;
+    *cluster = it->second.first;
+    *threads = it->second.second;
+    return true;
+}
+
+struct ProbeResult {
+    float ms;
+    std::vector<uint8_t> lattice;
+    long long state[kStateSlots];
+};
+
+// Runs n sweeps of the handle's lattice with launch shape (cluster, threads) on the
+// scratch lattice/state (copied from the handle first).
+klmc_status probe_shape(klmc_ctx *c, void *scratch_lat, long long *scratch_state, int cluster,
+                        int threads, int n, cudaEvent_t e0, cudaEvent_t e1, ProbeResult *out)
+{
+    SweepJob J = c->job;
+    J.lat = scratch_lat;
+    J.state = scratch_state;
+    for (int rep = 0; rep < 2; ++rep) {  // the first run warms up; the second is timed
+        KLMC_CUDA(cudaMemcpyAsync(scratch_lat, c->lat, c->lat_bytes, cudaMemcpyDeviceToDevice, c->stream));
+        KLMC_CUDA(cudaMemcpyAsync(scratch_state, c->state, kStateSlots * sizeof(long long),
+                                  cudaMemcpyDeviceToDevice, c->stream));
+        const long long base = c->sweep;
+        KLMC_CUDA(cudaMemcpyAsync(scratch_state + kSweepBase, &base, sizeof(base),
+                                  cudaMemcpyHostToDevice, c->stream));
+        KLMC_CUDA(cudaEventRecord(e0, c->stream));
+        if (cluster < 0) {
+            int dev = 0, sms = 0;
+            KLMC_CUDA(cudaGetDevice(&dev));
+            KLMC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+            KLMC_CUDA(configure_tiled());
+            KLMC_CUDA(launch_tiled_phases(J, tiled_band_rows(c->p.Ly, sms), 0, n, c->stream));
+            KLMC_CUDA(launch_advance(scratch_state, n, c->stream));
+        } else {
+            SweepCall call;
+            call.sweep0 = c->sweep;
+            call.n_mcs = n;
+            call.trace = nullptr;
+            call.trace_every = 0;
+            KLMC_CUDA(launch_resident_sweep_one(J, call, cluster, threads,
+                                                resident_smem_bytes(c->p.Lx, c->p.Ly, cluster),
+                                                c->stream));
+        }
+        KLMC_CUDA(cudaEventRecord(e1, c->stream));
+        KLMC_CUDA(cudaEventSynchronize(e1));
+    }
+    KLMC_CUDA(cudaEventElapsedTime(&out->ms, e0, e1));
+    out->lattice.resize(c->lat_bytes);
+    KLMC_CUDA(cudaMemcpy(out->lattice.data(), scratch_lat, c->lat_bytes, cudaMemcpyDeviceToHost));
+    KLMC_CUDA(cudaMemcpy(out->state, scratch_state, sizeof(out->state), cudaMemcpyDeviceToHost));
+    return KLMC_OK;
+}
+
+klmc_status autotune(klmc_ctx *c, int probe_sweeps)
+{
+    const TuneKey key{c->p.Lx, c->p.Ly, c->p.geometry, c->job.packing};
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            c->cluster = it->second.first;
+            c->threads = it->second.second;
+            return KLMC_OK;
+        }
+    }
+    std::vector<std::pair<int, int>> cands;
+    for (int C : {1, 2, 4, 8, 16}) {
+        if (C > 1 && c->p.Ly / C < 4) continue;
+        if (resident_smem_bytes(c->p.Lx, c->p.Ly, C) > (size_t)resident_max_smem_bytes()) continue;
+        if (C == 1) cands.push_back({1, 512});
+        cands.push_back({C, 256});
+    }
+    cands.push_back({-1, 256});
+    void *slat = dev_alloc(c, c->lat_bytes);
+    long long *sstate = (long long *)dev_alloc(c, kStateSlots * sizeof(long long));
+    if (!slat || !sstate) return fail(KLMC_ENOMEM, "autotune scratch allocation failed");
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    KLMC_CUDA(cudaEventCreate(&e0));
+    KLMC_CUDA(cudaEventCreate(&e1));
+    ProbeResult ref, cur;
+    float best_ms = 0.f;
+    std::pair<int, int> best = cands.front();
+    klmc_status st = KLMC_OK;
+    for (size_t i = 0; i < cands.size() && st == KLMC_OK; ++i) {
+        ProbeResult &r = i == 0 ? ref : cur;
+        st = probe_shape(c, slat, sstate, cands[i].first, cands[i].second, probe_sweeps, e0, e1, &r);
+        if (st != KLMC_OK) break;
+        if (i > 0) {
+            bool same = r.lattice == ref.lattice;
+            for (int k = kNUnlike; k <= kAccepts; ++k) same = same && r.state[k] == ref.state[k];
+            if (!same) {
+                st = fail(KLMC_ESTATE, "autotune: launch shape (" + std::to_string(cands[i].first) + ", " +
+                                           std::to_string(cands[i].second) +
+                                           ") changed the result; refusing it");
+                break;
+            }
+        }
+        if (i == 0 || r.ms < best_ms) {
+            best_ms = r.ms;
+            best = cands[i];
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != KLMC_OK) return st;
+    c->cluster = best.first;
+    c->threads = best.second;
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    g_tune_cache[key] = best;
     return KLMC_OK;
 }
 
@@ -581,11 +734,23 @@ klmc_status klmc_get_shape(klmc_ctx *c, int32_t *Lx, int32_t *Ly, int32_t *geome
     return KLMC_OK;
 }
 
+klmc_status klmc_autotune(klmc_ctx *c, int32_t probe_sweeps, int32_t *cluster, int32_t *threads)
+{
+    if (!c) return fail(KLMC_EINVAL, "ctx is NULL");
+    if (probe_sweeps < 1) return fail(KLMC_EINVAL, "probe_sweeps must be >= 1");
+    if (c->owner) return fail(KLMC_ESTATE, "replica views are tuned with their batch");
+    klmc_status st = autotune(c, probe_sweeps);
+    if (st != KLMC_OK) return st;
+    if (cluster) *cluster = c->cluster;
+    if (threads) *threads = c->threads;
+    return KLMC_OK;
+}
+
 klmc_status klmc_get_launch(klmc_ctx *c, int32_t *cluster, int32_t *threads_per_cta)
 {
     if (!c) return fail(KLMC_EINVAL, "ctx is NULL");
     if (cluster) *cluster = c->cluster;
-    if (threads_per_cta) *threads_per_cta = resident_threads(c->cluster);
+    if (threads_per_cta) *threads_per_cta = c->threads;
     return KLMC_OK;
 }
 
@@ -648,6 +813,50 @@ klmc_status klmc_batch_create(klmc_batch **out, const klmc_params *reps, int32_t
         return fail(KLMC_ECUDA, std::string("batch upload: ") + cudaGetErrorString(e));
     }
     b->hcalls.resize(n);
+    // Group replicas by cluster size (one launch per group, each on its own stream so
+    // the groups overlap on the GPU); inside a group, larger lattices first.
+    std::map<std::pair<int, int>, std::vector<int>> by_cluster;
+    for (int i = 0; i < n; ++i) by_cluster[{b->reps[i]->cluster, b->reps[i]->threads}].push_back(i);
+    b->dmap = (int *)dev_alloc(m, sizeof(int) * (size_t)n);
+    if (!b->dmap) {
+        klmc_batch_destroy(b);
+        return fail(KLMC_ENOMEM, "device allocation of the batch tables failed");
+    }
+    for (auto it = by_cluster.rbegin(); it != by_cluster.rend(); ++it) {
+        std::vector<int> &idx = it->second;
+        std::stable_sort(idx.begin(), idx.end(), [&](int a, int c) {
+            return b->reps[a]->N > b->reps[c]->N;
+        });
+        klmc_batch::Group g;
+        g.cluster = it->first.first;
+        g.threads = it->first.second;
+        g.offset = (int)b->hmap.size();
+        g.count = (int)idx.size();
+        g.smem = 0;
+        for (int i : idx) {
+            const size_t sm = resident_smem_bytes(b->reps[i]->p.Lx, b->reps[i]->p.Ly, g.cluster);
+            if (sm > g.smem) g.smem = sm;
+        }
+        g.stream = nullptr;
+        g.done = nullptr;
+        if (cudaStreamCreateWithFlags(&g.stream, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&g.done, cudaEventDisableTiming) != cudaSuccess) {
+            b->groups.push_back(g);
+            klmc_batch_destroy(b);
+            return fail(KLMC_ECUDA, "stream/event creation failed");
+        }
+        b->groups.push_back(g);
+        b->hmap.insert(b->hmap.end(), idx.begin(), idx.end());
+    }
+    e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->dmap, b->hmap.data(), sizeof(int) * (size_t)n, cudaMemcpyHostToDevice,
+                            b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) {
+        klmc_batch_destroy(b);
+        return fail(KLMC_ECUDA, std::string("batch groups: ") + cudaGetErrorString(e));
+    }
     *out = b;
     return KLMC_OK;
 }
@@ -656,7 +865,6 @@ klmc_status klmc_batch_sweep(klmc_batch *b, const int64_t *n_mcs)
 {
     if (!b || !n_mcs) return fail(KLMC_EINVAL, "NULL argument");
     const int n = (int)b->reps.size();
-    int cluster = 16;
     bool any = false;
     for (int i = 0; i < n; ++i) {
         if (n_mcs[i] < 0) return fail(KLMC_EINVAL, "n_mcs entries must be >= 0");
@@ -666,24 +874,24 @@ klmc_status klmc_batch_sweep(klmc_batch *b, const int64_t *n_mcs)
         call.n_mcs = n_mcs[i];
         call.trace = nullptr;
         call.trace_every = 0;
-        if (n_mcs[i] > 0) {
-            any = true;
-            if (c->cluster < cluster) cluster = c->cluster;
-        }
+        any = any || n_mcs[i] > 0;
     }
     if (!any) return KLMC_OK;
-    size_t smem = 0;
-    for (int i = 0; i < n; ++i) {
-        if (n_mcs[i] == 0) continue;
-        klmc_ctx *c = b->reps[i];
-        klmc_status st = check_resident(c, cluster);
-        if (st != KLMC_OK) return st;
-        const size_t s = resident_smem_bytes(c->p.Lx, c->p.Ly, cluster);
-        if (s > smem) smem = s;
-    }
     KLMC_CUDA(cudaMemcpyAsync(b->dcalls, b->hcalls.data(), sizeof(SweepCall) * (size_t)n,
                               cudaMemcpyHostToDevice, b->stream));
-    KLMC_CUDA(launch_resident_sweep(b->djobs, b->dcalls, n, cluster, smem, b->stream));
+    // Fork: every group stream waits for the call table; join: the batch stream
+    // waits for every group.
+    KLMC_CUDA(cudaEventRecord(b->fork, b->stream));
+    for (auto &g : b->groups) {
+        bool group_active = false;
+        for (int k = 0; k < g.count; ++k) group_active = group_active || n_mcs[b->hmap[g.offset + k]] > 0;
+        if (!group_active) continue;
+        KLMC_CUDA(cudaStreamWaitEvent(g.stream, b->fork, 0));
+        KLMC_CUDA(launch_resident_sweep(b->djobs, b->dcalls, b->dmap + g.offset, g.count, g.cluster,
+                                        g.threads, g.smem, g.stream));
+        KLMC_CUDA(cudaEventRecord(g.done, g.stream));
+        KLMC_CUDA(cudaStreamWaitEvent(b->stream, g.done, 0));
+    }
     for (int i = 0; i < n; ++i) b->reps[i]->sweep += n_mcs[i];
     return KLMC_OK;
 }
@@ -699,6 +907,15 @@ klmc_status klmc_batch_replica(klmc_batch *b, int32_t i, klmc_ctx **view)
 klmc_status klmc_batch_destroy(klmc_batch *b)
 {
     if (!b) return KLMC_OK;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    for (auto &g : b->groups) {
+        if (g.stream) {
+            cudaStreamSynchronize(g.stream);
+            cudaStreamDestroy(g.stream);
+        }
+        if (g.done) cudaEventDestroy(g.done);
+    }
+    if (b->fork) cudaEventDestroy(b->fork);
     // The batch tables were allocated on reps[0]; free them with it, last.
     for (size_t i = b->reps.size(); i-- > 0;) {
         klmc_ctx *c = b->reps[i];

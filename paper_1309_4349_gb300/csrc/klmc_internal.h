@@ -57,15 +57,18 @@ struct SweepCall {
 size_t resident_smem_bytes(int Lx, int Ly, int cluster);
 int resident_max_smem_bytes();
 int resident_max_cluster(int Ly);
-int resident_threads(int cluster);
+int resident_default_threads(int cluster);  // 512 for one CTA, else 256
 
-// Batched launch: one cluster of `cluster` CTAs per job, tables in device memory.
-// The trace buffers of the calls must be zeroed before the launch.
-cudaError_t launch_resident_sweep(const SweepJob *d_jobs, const SweepCall *d_calls, int n_jobs,
-                                  int cluster, size_t smem_bytes, cudaStream_t stream);
-// Single lattice: job and call passed by value as kernel parameters.
+// Batched launch: one cluster of `cluster` CTAs per job, tables in device memory;
+// launched job i is d_jobs[d_map[i]] (d_map null: job i).  The trace buffers of
+// the calls must be zeroed before the launch.
+cudaError_t launch_resident_sweep(const SweepJob *d_jobs, const SweepCall *d_calls,
+                                  const int *d_map, int n_jobs, int cluster, int threads,
+                                  size_t smem_bytes, cudaStream_t stream);
+// Single lattice: job and call passed by value as kernel parameters.  threads is
+// 512 or 256.
 cudaError_t launch_resident_sweep_one(const SweepJob &job, const SweepCall &call, int cluster,
-                                      size_t smem_bytes, cudaStream_t stream);
+                                      int threads, size_t smem_bytes, cudaStream_t stream);
 
 // Tiled path for lattices too large for shared memory: one launch per phase,
 // CTAs of H-row bands (tiled_band_rows), sweep index read from state[kSweepBase].

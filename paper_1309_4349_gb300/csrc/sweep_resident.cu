@@ -226,10 +226,10 @@ __device__ __forceinline__ uint32_t cluster_ctarank()
     return v;
 }
 
-template <int THREADS>
-__global__ void __launch_bounds__(THREADS, 1)
+template <int THREADS, int MINB>
+__global__ void __launch_bounds__(THREADS, MINB)
 resident_sweep_kernel(const SweepJob *__restrict__ jobs, const SweepCall *__restrict__ calls,
-                      const SweepJob job0, const SweepCall call0)
+                      const int *__restrict__ job_map, const SweepJob job0, const SweepCall call0)
 {
     constexpr int kWarps = THREADS / 32;
     extern __shared__ __align__(16) uint32_t lat[];
@@ -239,7 +239,7 @@ resident_sweep_kernel(const SweepJob *__restrict__ jobs, const SweepCall *__rest
 
     const int C = (int)cluster_nctarank();
     const int rank = (int)cluster_ctarank();
-    const int job = (int)blockIdx.x / C;
+    const int job = job_map ? job_map[blockIdx.x / C] : (int)blockIdx.x / C;
     const SweepJob &J = jobs ? jobs[job] : job0;
     const SweepCall Cl = calls ? calls[job] : call0;
     if (Cl.n_mcs <= 0) return;  // uniform over the cluster
@@ -357,10 +357,9 @@ resident_sweep_kernel(const SweepJob *__restrict__ jobs, const SweepCall *__rest
     }
 }
 
-constexpr int kThreadsSingle = 512;
-constexpr int kThreadsCluster = 256;
-
-template <int THREADS>
+// Two variants: 512 threads (one CTA per SM; single lattices on one CTA) and 256
+// threads with at most 128 registers (two CTAs per SM; clusters and batches).
+template <int THREADS, int MINB>
 cudaError_t configure_once()
 {
     static thread_local int configured_device = -1;
@@ -368,18 +367,18 @@ cudaError_t configure_once()
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (configured_device == dev) return cudaSuccess;
-    e = cudaFuncSetAttribute(resident_sweep_kernel<THREADS>,
+    e = cudaFuncSetAttribute(resident_sweep_kernel<THREADS, MINB>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, resident_max_smem_bytes());
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(resident_sweep_kernel<THREADS>,
+        e = cudaFuncSetAttribute(resident_sweep_kernel<THREADS, MINB>,
                                  cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e == cudaSuccess) configured_device = dev;
     return e;
 }
 
-cudaError_t launch(const SweepJob *d_jobs, const SweepCall *d_calls, const SweepJob &job0,
-                   const SweepCall &call0, int n_jobs, int cluster, size_t smem_bytes,
-                   cudaStream_t stream)
+cudaError_t launch(const SweepJob *d_jobs, const SweepCall *d_calls, const int *d_map,
+                   const SweepJob &job0, const SweepCall &call0, int n_jobs, int cluster,
+                   int threads, size_t smem_bytes, cudaStream_t stream)
 {
     cudaLaunchConfig_t cfg;
     memset(&cfg, 0, sizeof(cfg));
@@ -394,16 +393,16 @@ cudaError_t launch(const SweepJob *d_jobs, const SweepCall *d_calls, const Sweep
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     cudaError_t e;
-    if (cluster == 1) {
-        e = configure_once<kThreadsSingle>();
+    if (threads == 512) {
+        e = configure_once<512, 1>();
         if (e != cudaSuccess) return e;
-        cfg.blockDim = dim3(kThreadsSingle, 1, 1);
-        e = cudaLaunchKernelEx(&cfg, resident_sweep_kernel<kThreadsSingle>, d_jobs, d_calls, job0, call0);
+        cfg.blockDim = dim3(512, 1, 1);
+        e = cudaLaunchKernelEx(&cfg, resident_sweep_kernel<512, 1>, d_jobs, d_calls, d_map, job0, call0);
     } else {
-        e = configure_once<kThreadsCluster>();
+        e = configure_once<256, 2>();
         if (e != cudaSuccess) return e;
-        cfg.blockDim = dim3(kThreadsCluster, 1, 1);
-        e = cudaLaunchKernelEx(&cfg, resident_sweep_kernel<kThreadsCluster>, d_jobs, d_calls, job0, call0);
+        cfg.blockDim = dim3(256, 1, 1);
+        e = cudaLaunchKernelEx(&cfg, resident_sweep_kernel<256, 2>, d_jobs, d_calls, d_map, job0, call0);
     }
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
@@ -430,7 +429,7 @@ int resident_max_smem_bytes()
     return 227 * 1024 - 3072;
 }
 
-int resident_threads(int cluster) { return cluster == 1 ? kThreadsSingle : kThreadsCluster; }
+int resident_default_threads(int cluster) { return cluster == 1 ? 512 : 256; }
 
 int resident_max_cluster(int Ly)
 {
@@ -439,21 +438,23 @@ int resident_max_cluster(int Ly)
     return c;
 }
 
-cudaError_t launch_resident_sweep(const SweepJob *d_jobs, const SweepCall *d_calls, int n_jobs,
-                                  int cluster, size_t smem_bytes, cudaStream_t stream)
+cudaError_t launch_resident_sweep(const SweepJob *d_jobs, const SweepCall *d_calls,
+                                  const int *d_map, int n_jobs, int cluster, int threads,
+                                  size_t smem_bytes, cudaStream_t stream)
 {
     if (n_jobs <= 0) return cudaSuccess;
     SweepJob none_job;
     SweepCall none_call;
     memset(&none_job, 0, sizeof(none_job));
     memset(&none_call, 0, sizeof(none_call));
-    return launch(d_jobs, d_calls, none_job, none_call, n_jobs, cluster, smem_bytes, stream);
+    return launch(d_jobs, d_calls, d_map, none_job, none_call, n_jobs, cluster, threads, smem_bytes,
+                  stream);
 }
 
 cudaError_t launch_resident_sweep_one(const SweepJob &job, const SweepCall &call, int cluster,
-                                      size_t smem_bytes, cudaStream_t stream)
+                                      int threads, size_t smem_bytes, cudaStream_t stream)
 {
-    return launch(nullptr, nullptr, job, call, 1, cluster, smem_bytes, stream);
+    return launch(nullptr, nullptr, nullptr, job, call, 1, cluster, threads, smem_bytes, stream);
 }
 
 }  // namespace klmc

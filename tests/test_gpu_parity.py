@@ -142,6 +142,29 @@ def test_8192_lattice_tiled():
     assert lat.counters()["sweeps"] == 26
 
 
+@pytest.mark.parametrize("geometry", GEOMS)
+@pytest.mark.parametrize("Lx,Ly,nA,bw", [(64, 64, 2048, 0.6), (150, 97, 4000, 1.0), (23, 41, 300, -0.3)])
+def test_autotune_keeps_trajectory(geometry, Lx, Ly, nA, bw):
+    """Tuning times every valid launch shape on a scratch copy (all must agree) and
+    leaves the lattice, its counters and its future trajectory unchanged."""
+    seed = 300 + Lx
+    lat = make(Lx, Ly, nA, bw, seed, geometry)
+    lat.sweep(3)
+    before = lat.get_lattice()
+    cnt = lat.counters()
+    cluster, threads = lat.autotune(4)
+    assert (cluster, threads) == lat.launch_shape()
+    assert cluster == -1 or cluster in (1, 2, 4, 8, 16)
+    assert threads in (256, 512)
+    assert np.array_equal(lat.get_lattice(), before)
+    assert lat.counters() == cnt
+    lat.sweep(9)
+    ref = oracle.run(Lx, Ly, geometry, bw, seed, oracle.init(Lx, Ly, nA, seed), 0, 12)
+    assert_same_run(lat, ref)
+    # a new lattice of the same shape picks the tuned shape up
+    assert make(Lx, Ly, nA, bw, seed + 1, geometry).launch_shape() == (cluster, threads)
+
+
 def test_cluster_size_rejected():
     with pytest.raises(klmc.KlmcError) as e:
         make(16, 16, 100, 0.5, 1, cluster=8)  # bands of 2 rows
