@@ -59,6 +59,23 @@ C_PHILOX = 40.0
 # paper_1309_4349_gb300/probes/int_peak.cu measures 60 LOP3 and 30 IMAD.WIDE
 # (+30 LOP3) lane-ops/clk/SM on GB300, i.e. one 64-lane integer pipe.
 INT32_LANES_PER_SM = 64
+# DRAM bytes (read + write) of one resident-sweep launch of this workload from one ncu
+# capture (profiles/resident_sweep_400x400x5_ncu.md), valid only for the kernel
+# sources it was taken with (hash of sweep_resident.cu + sweep_common.cuh).
+TRAFFIC_C2_LAUNCH = 229888
+TRAFFIC_C2_SOURCES = "137a4d9e64557aa8"
+
+
+def resident_sources_hash() -> str:
+    import hashlib
+
+    h = hashlib.sha256()
+    for f in ("sweep_resident.cu", "sweep_common.cuh"):
+        with open(os.path.join(ROOT, "paper_1309_4349_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 # Kernels launched per library call (fixed by the library's structure).
 LAUNCHES_SWEEP = 1
 LAUNCHES_HISTOGRAM = 5
@@ -72,8 +89,11 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--mcs", type=int, default=N_MCS, help="steps per run (default: the workload's)")
-    ap.add_argument("--workload", choices=["c2", "c1", "c3", "c4"], default="c2",
-                    help="c2 (default): 400x400 x 5 omega; c1: 64x64; c3: 8192x8192; c4: 256 replicas")
+    ap.add_argument("--workload", choices=["c2", "c1", "c3", "c4", "c5"], default="c2",
+                    help="c2 (default): 400x400 x 5 omega; c1: 64x64; c3: 8192x8192; c4: 256 replicas; "
+                         "c5: serving")
+    ap.add_argument("--jobs", type=int, default=300, help="c5: number of jobs")
+    ap.add_argument("--rate", type=float, default=0.0, help="c5: arrivals per second (0: 0.8 load)")
     ap.add_argument("--skip-plain", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     return ap.parse_args()
@@ -211,6 +231,68 @@ C1 = dict(L=64, n_A=2048, omega=0.6, seed=1, mcs=1000, hist_every=100)
 C3 = dict(L=8192, omega=0.85, seed=7, mcs=1000, trace_every=10)
 C4 = dict(n=256, L_min=100, L_max=1024, f_min=0.1, f_max=0.5, w_min=0.1, w_max=1.2, mcs=5000,
           seed0=1000, draw_seed=20260)
+C5 = dict(L_min=64, L_max=2048, f_min=0.1, f_max=0.5, w_min=0.1, w_max=1.2, mcs_min=1e3, mcs_max=1e5,
+          seed0=1000000, draw_seed=77, budget=16 << 30)
+
+
+def c5_jobs(n):
+    """Serving jobs: side log-uniform over [64, 2048], A fraction U[0.1, 0.5],
+    omega/kT U[0.1, 1.2], steps log-uniform over [1e3, 1e5], seed 10^6 + j."""
+    import numpy as np
+
+    rng = np.random.default_rng(C5["draw_seed"])
+    jobs = []
+    for j in range(n):
+        L = int(round(float(np.exp(rng.uniform(np.log(C5["L_min"]), np.log(C5["L_max"]))))))
+        mcs = int(round(float(np.exp(rng.uniform(np.log(C5["mcs_min"]), np.log(C5["mcs_max"]))))))
+        jobs.append(dict(L=L, fraction_A=float(rng.uniform(C5["f_min"], C5["f_max"])),
+                         omega_over_kT=float(rng.uniform(C5["w_min"], C5["w_max"])), n_mcs=mcs,
+                         seed=C5["seed0"] + j))
+    return jobs
+
+
+def bench_serving(args, klmc, np):
+    """Poisson arrivals submitted in real time from a host thread; every job is
+    admitted by memory, kept resident and batched with the others in rounds."""
+    jobs = c5_jobs(args.jobs)
+    mean_attempts = float(np.mean([j["L"] ** 2 * j["n_mcs"] for j in jobs]))
+    rate = args.rate if args.rate > 0 else 0.8 * 1.5e11 / mean_attempts
+    rng = np.random.default_rng(C5["draw_seed"] + 1)
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=len(jobs)))
+    srv = klmc.Server(C5["budget"])
+    ids = [None] * len(jobs)
+    t0 = time.perf_counter()
+    for k, (j, t) in enumerate(zip(jobs, arrivals)):
+        wait = t - (time.perf_counter() - t0)
+        if wait > 0:
+            time.sleep(wait)
+        ids[k] = srv.submit(j["L"], j["L"], n_mcs=j["n_mcs"], fraction_A=j["fraction_A"],
+                            omega_over_kT=j["omega_over_kT"], seed=j["seed"])
+    srv.drain(24 * 3600)
+    makespan = time.perf_counter() - t0
+    res = [srv.poll(i) for i in ids]
+    st = srv.stats()
+    srv.close()
+    assert all(r["status"] == 0 for r in res)
+    lat = np.array([r["finish_s"] - r["submit_s"] for r in res])
+    wait = np.array([r["start_s"] - r["submit_s"] for r in res])
+    attempts = sum(r["attempts"] for r in res)
+    return {
+        "metric": "Kawasaki exchange attempts/s", "value": attempts / makespan, "unit": "attempts/s",
+        "n_gpus": 1, "steps": 1, "warmup": 0, "ms_per_step": makespan * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": f"serving: Poisson arrivals of {len(jobs)} jobs (the configuration's "
+                               "10000 reduced to bound the run), side log-uniform 64-2048, A fraction "
+                               "U[0.1,0.5], omega/kT U[0.1,1.2], MCS log-uniform 1e3-1e5, seeds 1e6+j",
+                   "arrival_rate_per_s": rate, "offered_load_attempts_per_s": rate * mean_attempts,
+                   "device_budget_bytes": C5["budget"],
+                   "form": "job server: memory admission, resident lattices, rounds over all resident jobs"},
+        "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                      "mean": float(lat.mean()), "max": float(lat.max())},
+        "queue_wait_s": {"p50": float(np.percentile(wait, 50)), "p99": float(np.percentile(wait, 99))},
+        "server": {k: st[k] for k in ("rounds", "busy_s", "uptime_s", "peak_device_bytes")},
+        "jobs": len(jobs), "attempts": attempts,
+    }
 
 
 def c4_replicas():
@@ -422,6 +504,10 @@ def main():
             dist.barrier()
 
     klmc.build()
+    if args.workload == "c5":
+        if rank == 0:
+            print(json.dumps(bench_serving(args, klmc, np)), flush=True)
+        return
     if args.workload != "c2":
         if rank == 0:
             bench_other(args, klmc, torch, np)
@@ -530,7 +616,12 @@ def main():
     ctas = nrun * cluster
     roofline = {"bound": "alu", "kernel": "resident_sweep_kernel", "achieved": achieved_tops,
                 "peak": peak_tops, "unit": "Tops/s (INT32 lane-ops)", "frac": achieved_tops / peak_tops,
-                "traffic": None, "ops_per_attempt": ops_attempt, "p_draw": p_draw,
+                "traffic": (TRAFFIC_C2_LAUNCH if resident_sources_hash() == TRAFFIC_C2_SOURCES
+                            and n_mcs % HIST_EVERY == 0 else None),
+                "traffic_note": "DRAM bytes per launch from one ncu capture (cold cache); the "
+                                "lattices stay in shared memory within a launch",
+                "algorithmic_bytes_per_launch": 2 * nrun * L * ((L + 31) // 32) * 4,
+                "ops_per_attempt": ops_attempt, "p_draw": p_draw,
                 "launch_ms": launch_ms, "attempts_per_launch": attempts_launch,
                 "ctas_per_launch": ctas, "cluster": cluster, "threads_per_cta": threads,
                 "sm_count": sm_count,

@@ -230,6 +230,73 @@ klmc_status klmc_batch_replica(klmc_batch *b, int32_t i, klmc_ctx **view);
 /* Frees the batch and its replicas.  NULL is accepted. */
 klmc_status klmc_batch_destroy(klmc_batch *b);
 
+/* ------------------------------------------------------------------------ */
+/* Serving form: a job server with continuous batching.                      */
+/* ------------------------------------------------------------------------ */
+typedef struct klmc_server klmc_server;
+
+enum { KLMC_JOB_KEEP_LATTICE = 1 }; /* submit flag: keep the final lattice on the host */
+
+typedef struct klmc_job_result {
+    int32_t status;        /* KLMC_OK, or the error that ended the job              */
+    int32_t reserved;
+    int64_t n_mcs;         /* Monte Carlo steps run                                 */
+    int64_t n_unlike;      /* final number of unlike contacts                       */
+    int64_t attempts, unlike, draws, accepts;  /* exact counters of the job          */
+    double submit_s;       /* submission, admission and completion times, seconds   */
+    double start_s;        /* since the server was created (host steady clock)      */
+    double finish_s;
+    int64_t n_histograms;  /* A-cluster histograms taken (hist_every cadence + end) */
+} klmc_job_result;
+
+typedef struct klmc_server_stats {
+    int64_t submitted, finished, queued, resident, rounds, attempts;
+    double busy_s, uptime_s;
+    int64_t device_bytes, peak_device_bytes;
+} klmc_server_stats;
+
+/* Starts a server whose resident jobs may hold at most device_mem_budget bytes of
+ * device memory.  stream: cudaStream_t for the server's work (NULL: a private
+ * stream).  Jobs are admitted in arrival order while their memory fits both the
+ * budget and the device's free memory; admitted lattices stay resident until their
+ * job finishes.  Every round advances all resident jobs together (one
+ * resident-kernel launch per launch shape), each by a number of steps sized to
+ * take about the same time; finished jobs leave and queued jobs join between
+ * rounds.  A job's result does not depend on the other jobs. */
+klmc_status klmc_server_create(klmc_server **out, size_t device_mem_budget, void *stream);
+
+/* Queues a job: the lattice of p (p->stream, alloc and free are ignored), n_mcs
+ * steps, an A-cluster histogram every hist_every steps and at the end
+ * (0: none), flags (KLMC_JOB_KEEP_LATTICE).  Thread-safe; never blocks on GPU work.
+ * Jobs too large for the budget finish with status KLMC_EINVAL. */
+klmc_status klmc_server_submit(klmc_server *s, const klmc_params *p, int64_t n_mcs,
+                               int64_t hist_every, uint32_t flags, uint64_t *job_id);
+
+/* Result of a job; KLMC_EBUSY while it is queued or running. */
+klmc_status klmc_server_poll(klmc_server *s, uint64_t job_id, klmc_job_result *out);
+
+/* Final lattice (one byte per site) of a finished job submitted with
+ * KLMC_JOB_KEEP_LATTICE. */
+klmc_status klmc_server_job_lattice(klmc_server *s, uint64_t job_id, uint8_t *host_out, int64_t n);
+
+/* Last A-cluster histogram of a finished job (sparse, ascending); ETRUNC with
+ * *n_distinct = needed length when capacity is too small. */
+klmc_status klmc_server_job_histogram(klmc_server *s, uint64_t job_id, int64_t *sizes, int64_t *counts,
+                                      int64_t capacity, int64_t *n_distinct);
+
+/* Forgets a finished job's stored results. */
+klmc_status klmc_server_release(klmc_server *s, uint64_t job_id);
+
+/* Server counters (jobs, rounds, attempts of finished jobs, busy time, memory). */
+klmc_status klmc_server_get_stats(klmc_server *s, klmc_server_stats *out);
+
+/* Waits until every submitted job has finished; ETIMEOUT after timeout_s seconds. */
+klmc_status klmc_server_drain(klmc_server *s, double timeout_s);
+
+/* Finishes the queued and resident jobs, stops the worker and frees everything.
+ * NULL is accepted. */
+klmc_status klmc_server_destroy(klmc_server *s);
+
 /* Human-readable name of a status. */
 const char *klmc_status_str(klmc_status s);
 

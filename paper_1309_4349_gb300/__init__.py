@@ -45,6 +45,30 @@ class Counters(ctypes.Structure):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}
 
 
+class JobResult(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("reserved", ctypes.c_int32), ("n_mcs", ctypes.c_int64),
+                ("n_unlike", ctypes.c_int64), ("attempts", ctypes.c_int64), ("unlike", ctypes.c_int64),
+                ("draws", ctypes.c_int64), ("accepts", ctypes.c_int64), ("submit_s", ctypes.c_double),
+                ("start_s", ctypes.c_double), ("finish_s", ctypes.c_double),
+                ("n_histograms", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("finished", ctypes.c_int64), ("queued", ctypes.c_int64),
+                ("resident", ctypes.c_int64), ("rounds", ctypes.c_int64), ("attempts", ctypes.c_int64),
+                ("busy_s", ctypes.c_double), ("uptime_s", ctypes.c_double),
+                ("device_bytes", ctypes.c_int64), ("peak_device_bytes", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+JOB_KEEP_LATTICE = 1
+
+
 class KlmcError(RuntimeError):
     def __init__(self, status: int, message: str):
         self.status = status
@@ -96,6 +120,15 @@ def lib():
         "klmc_batch_sweep": [vp, P(i64)],
         "klmc_batch_replica": [vp, i32, P(vp)],
         "klmc_batch_destroy": [vp],
+        "klmc_server_create": [P(vp), ctypes.c_size_t, vp],
+        "klmc_server_submit": [vp, P(Params), i64, i64, ctypes.c_uint32, P(u64)],
+        "klmc_server_poll": [vp, u64, P(JobResult)],
+        "klmc_server_job_lattice": [vp, u64, vp, i64],
+        "klmc_server_job_histogram": [vp, u64, vp, vp, i64, P(i64)],
+        "klmc_server_release": [vp, u64],
+        "klmc_server_get_stats": [vp, P(ServerStats)],
+        "klmc_server_drain": [vp, dbl],
+        "klmc_server_destroy": [vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -329,6 +362,73 @@ class Batch:
             for r in self.replicas:
                 r._h = None
             _check(lib().klmc_batch_destroy(self._h))
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Job server with continuous batching (klmc_server): jobs are admitted by
+    device memory, stay resident, and advance together in rounds."""
+
+    def __init__(self, device_mem_budget: int, stream=None):
+        h = ctypes.c_void_p()
+        sh = None if stream is None else int(stream.cuda_stream)
+        _check(lib().klmc_server_create(ctypes.byref(h), int(device_mem_budget), sh))
+        self._h = h
+
+    def submit(self, Lx: int, Ly: int | None = None, *, n_mcs: int, hist_every: int = 0,
+               keep_lattice: bool = False, geometry: int = TRI6, packing: int = PACK_BIT,
+               n_A: int = -1, fraction_A: float = 0.5, omega_over_kT: float = 0.0, seed: int = 1,
+               cluster: int = 0) -> int:
+        p = make_params(Lx, Ly, geometry=geometry, packing=packing, n_A=n_A, fraction_A=fraction_A,
+                        omega_over_kT=omega_over_kT, seed=seed, cluster=cluster)
+        jid = ctypes.c_uint64()
+        _check(lib().klmc_server_submit(self._h, ctypes.byref(p), int(n_mcs), int(hist_every),
+                                        JOB_KEEP_LATTICE if keep_lattice else 0, ctypes.byref(jid)))
+        return int(jid.value)
+
+    def poll(self, job_id: int):
+        """Result dict of a finished job, or None while it is queued or running."""
+        r = JobResult()
+        st = lib().klmc_server_poll(self._h, int(job_id), ctypes.byref(r))
+        if st == 5:  # KLMC_EBUSY
+            return None
+        _check(st)
+        return r.as_dict()
+
+    def lattice(self, job_id: int, n: int) -> np.ndarray:
+        out = np.zeros(n, dtype=np.uint8)
+        _check(lib().klmc_server_job_lattice(self._h, int(job_id), out.ctypes.data, n))
+        return out
+
+    def histogram(self, job_id: int):
+        cap = 1 << 16
+        sizes = np.zeros(cap, dtype=np.int64)
+        counts = np.zeros(cap, dtype=np.int64)
+        n = ctypes.c_int64()
+        _check(lib().klmc_server_job_histogram(self._h, int(job_id), sizes.ctypes.data,
+                                               counts.ctypes.data, cap, ctypes.byref(n)))
+        return sizes[:n.value].copy(), counts[:n.value].copy()
+
+    def release(self, job_id: int):
+        _check(lib().klmc_server_release(self._h, int(job_id)))
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        _check(lib().klmc_server_get_stats(self._h, ctypes.byref(st)))
+        return st.as_dict()
+
+    def drain(self, timeout_s: float = 3600.0):
+        _check(lib().klmc_server_drain(self._h, float(timeout_s)))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _check(lib().klmc_server_destroy(self._h))
             self._h = None
 
     def __del__(self):

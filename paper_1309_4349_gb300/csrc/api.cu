@@ -60,52 +60,7 @@ bool device_ok(std::string *why)
 
 void klmc::set_last_error(const char *msg) { g_err = msg ? msg : ""; }
 
-struct klmc_ctx {
-    klmc_params p;
-    long long N = 0, nA = 0;
-    bool nA_on_device = false;    // nA must be read back from state[kNA]
-    int W = 0, pitch = 0;
-    int cluster = 1;              // CTAs per lattice in the resident sweep (-1: tiled path)
-    int threads = 512;            // threads per CTA of the resident sweep (512 or 256)
-    size_t lat_bytes = 0;
-    void *lat = nullptr;
-    long long *state = nullptr;   // StateSlot array
-    void *init_scratch = nullptr;
-    long long sweep = 0;
-    SweepJob job;                 // host copy of the static job
-    cudaStream_t stream = nullptr;
-    void *cluster_mem = nullptr;  // lazily: ClusterScratch + host-API output
-    ClusterScratch cs;
-    long long *hist_out = nullptr;
-    long long hist_cap = 0;
-    uint8_t *dbytes = nullptr;    // lazily: one byte per site
-    klmc_batch *owner = nullptr;  // non-null for replica views
-    std::vector<std::pair<void *, size_t>> allocs;
-    // tiled path: band height, capture stream, and instantiated graphs of K sweeps
-    int tiled_H = 0;
-    cudaStream_t capture_stream = nullptr;
-    std::map<int, cudaGraphExec_t> graphs;
-};
-
-struct klmc_batch {
-    std::vector<klmc_ctx *> reps;
-    SweepJob *djobs = nullptr;
-    SweepCall *dcalls = nullptr;
-    int *dmap = nullptr;            // replica indices grouped by cluster size, largest first
-    std::vector<SweepCall> hcalls;
-    cudaStream_t stream = nullptr;
-    klmc_ctx *mem_owner = nullptr;  // holds the batch arrays' allocations
-    // groups of replicas sharing a cluster size: (cluster, offset into dmap, count)
-    struct Group {
-        int cluster, threads, offset, count;
-        size_t smem;
-        cudaStream_t stream;
-        cudaEvent_t done;
-    };
-    std::vector<Group> groups;
-    std::vector<int> hmap;
-    cudaEvent_t fork = nullptr;
-};
+#include "klmc_host.h"
 
 namespace {
 
@@ -227,7 +182,7 @@ klmc_status ensure_clusters(klmc_ctx *c)
 
 bool tuned_shape(int Lx, int Ly, int geometry, int packing, int *cluster, int *threads);
 
-klmc_status create_one(klmc_ctx **out, const klmc_params *p, klmc_batch *owner)
+klmc_status create_one(klmc_ctx **out, const klmc_params *p, klmc_batch *owner, bool sync = true)
 {
     klmc_status st = validate(p);
     if (st != KLMC_OK) return st;
@@ -290,7 +245,7 @@ klmc_status create_one(klmc_ctx **out, const klmc_params *p, klmc_batch *owner)
     if (e == cudaSuccess)
         e = launch_recount(c->lat, J.packing, p->Lx, p->Ly, c->pitch, p->geometry,
                            c->state + kNUnlike, c->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e == cudaSuccess && sync) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {
         free_all(c);
         delete c;
@@ -535,6 +490,25 @@ klmc_status autotune(klmc_ctx *c, int probe_sweeps)
 }
 
 }  // namespace
+
+klmc_status klmc::host::create_async(klmc_ctx **out, const klmc_params *p)
+{
+    return create_one(out, p, nullptr, false);
+}
+
+void klmc::host::destroy(klmc_ctx *c)
+{
+    free_all(c);
+    delete c;
+}
+
+size_t klmc::host::device_bytes(const klmc_params *p)
+{
+    const size_t W = (size_t)(p->Lx + 31) / 32;
+    const size_t lat = p->packing == KLMC_PACK_BYTE ? (size_t)((p->Lx + 15) / 16 * 16) * (size_t)p->Ly
+                                                    : (W + 3) / 4 * 16 * (size_t)p->Ly;
+    return lat + kStateSlots * sizeof(long long) + init_scratch_bytes() + 3 * 256;
+}
 
 extern "C" {
 

@@ -274,10 +274,8 @@ cudaError_t launch_init_lattice(void *lat, int packing, int Lx, int Ly, int pitc
         SelectState h;
         memset(&h, 0, sizeof(h));
         h.k = nA;
+        // From pageable memory: the copy is staged before cudaMemcpyAsync returns.
         e = cudaMemcpyAsync(st, &h, sizeof(SelectState), cudaMemcpyHostToDevice, stream);
-        if (e != cudaSuccess) return e;
-        // The host copy above is pageable; make sure it has been consumed before h dies.
-        e = cudaStreamSynchronize(stream);
         if (e != cudaSuccess) return e;
         const int g = grid_for(N, kBlock * 8);
         for (int pass = 0; pass < 12; ++pass) {
