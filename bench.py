@@ -435,10 +435,6 @@ def bench_other(args, klmc, torch, np):
         reps = c4_replicas()
         b = klmc.Batch([dict(r, packing=klmc.PACK_BIT) for r in reps])
         inits = [torch.from_numpy(l.get_lattice()).cuda() for l in b.replicas]
-        groups = {}
-        for l in b.replicas:
-            C, _ = l.launch_shape()
-            groups[C] = groups.get(C, 0) + 1
 
         def step():
             for l, t in zip(b.replicas, inits):
@@ -452,12 +448,17 @@ def bench_other(args, klmc, torch, np):
         attempts = sum(x["attempts"] for x in cnts)
         draws = sum(x["draws"] for x in cnts)
         ms_step = sum(ms) / len(ms)
-        ctas = sum(C * n for C, n in groups.items())
+        groups = {}  # launch shape (CTAs per replica x threads per CTA) the timed calls used
+        for i in range(len(reps)):
+            C, T = b.launch_shape(i)
+            groups[(C, T)] = groups.get((C, T), 0) + 1
+        ctas = sum(C * n for (C, _), n in groups.items())
         line.update({"value": attempts / (ms_step * 1e-3), "ms_per_step": ms_step,
                      "config": {"workload": "batched: 256 replicas, side log-uniform 100-1024, A "
                                 "fraction U[0.1,0.5], omega/kT U[0.1,1.2], seeds 1000+r, 5000 MCS each",
-                                "form": "batched: one launch per cluster-size group, groups on "
-                                        "concurrent streams", "groups": {str(k): v for k, v in groups.items()},
+                                "form": "batched: one launch per launch shape, launches on concurrent "
+                                        "streams",
+                                "groups": {f"{C}x{T}": v for (C, T), v in sorted(groups.items())},
                                 "l2": "flushed between steps"},
                      "roofline": _roofline("resident_sweep_kernel", ms_step, attempts, draws / attempts,
                                            sm_count, clk["sm_mhz"] if clk else 2070.0, ctas,

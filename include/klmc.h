@@ -62,7 +62,11 @@ typedef struct klmc_params {
     int32_t packing;       /* device store: KLMC_PACK_BIT (1 bit/site), _BYTE, or
                               _AUTO (= BIT)                                       */
     int32_t cluster;       /* CTAs that share one lattice in the resident sweep
-                              (a thread-block cluster, 1..16); 0 = automatic      */
+                              (a thread-block cluster, 1..16); -1 = tiled per-phase
+                              path; 0 = automatic                                 */
+    int32_t threads;       /* threads per CTA of the resident sweep: 128, 256 or
+                              512 (one CTA per lattice only); 0 = automatic        */
+    int32_t reserved0;
     int64_t n_A;           /* number of A lipids; -1 = floor(fraction_A*N + 0.5)  */
     double fraction_A;     /* used when n_A < 0; in [0, 1]                        */
     double omega_over_kT;  /* omega_AB / kT, finite; E/kT = omega/kT * n_unlike   */
@@ -212,16 +216,26 @@ klmc_status klmc_synchronize(klmc_ctx *c);
 klmc_status klmc_destroy(klmc_ctx *c);
 
 /* Batched form: n independent replicas (own sizes, compositions, omega, seeds)
- * advanced together by the resident kernel, one thread-block cluster per replica
- * (each replica's own cluster size, params.cluster or automatic).  Replicas that
- * share a cluster size form one launch, larger lattices first; the launches of
- * different sizes run on internal streams forked from and joined back to the
- * stream of reps[0], which every replica uses.  Every replica must fit the
+ * advanced together by the resident kernel, one thread-block cluster per replica.
+ * Each call chooses the launch shapes of the replicas it advances: a replica with
+ * a fixed shape (params.cluster or params.threads set) keeps it; replicas with
+ * automatic shapes keep theirs (tuned, else automatic) while the call's CTAs fit
+ * the GPU's SMs, and otherwise run at half the CTAs per replica (where the band
+ * still fits shared memory) with 128 threads per CTA, so that several CTAs share
+ * an SM.  Replicas of one shape form one launch, larger lattices first; the
+ * launches of different shapes run on internal streams forked from and joined
+ * back to the stream of reps[0], which every replica uses.  The trajectory of a
+ * replica does not depend on its launch shape.  Every replica must fit the
  * shared-memory resident sweep. */
 klmc_status klmc_batch_create(klmc_batch **out, const klmc_params *reps, int32_t n);
 
 /* Enqueues n_mcs[i] steps for replica i (entries may differ; 0 skips). */
 klmc_status klmc_batch_sweep(klmc_batch *b, const int64_t *n_mcs);
+
+/* Launch shape (CTAs per replica, threads per CTA) replica i ran with in the last
+ * klmc_batch_sweep that advanced it; before that, the replica's own shape.  Either
+ * pointer may be NULL.  EINVAL for an index out of range. */
+klmc_status klmc_batch_get_launch(klmc_batch *b, int32_t i, int32_t *cluster, int32_t *threads_per_cta);
 
 /* Borrowed handle of replica i, usable with every per-lattice call except
  * klmc_destroy; valid until klmc_batch_destroy. */
@@ -260,9 +274,11 @@ typedef struct klmc_server_stats {
  * stream).  Jobs are admitted in arrival order while their memory fits both the
  * budget and the device's free memory; admitted lattices stay resident until their
  * job finishes.  Every round advances all resident jobs together (one
- * resident-kernel launch per launch shape), each by a number of steps sized to
- * take about the same time; finished jobs leave and queued jobs join between
- * rounds.  A job's result does not depend on the other jobs. */
+ * resident-kernel launch per launch shape, shapes chosen per round as for a batch
+ * (klmc_batch_create), except that the jobs whose remaining steps take longest
+ * keep their own shapes while their CTAs fit the SMs), each by a number of steps
+ * sized to take about the same time; finished jobs leave and queued jobs join
+ * between rounds.  A job's result does not depend on the other jobs. */
 klmc_status klmc_server_create(klmc_server **out, size_t device_mem_budget, void *stream);
 
 /* Queues a job: the lattice of p (p->stream, alloc and free are ignored), n_mcs

@@ -30,7 +30,8 @@ FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void
 class Params(ctypes.Structure):
     _fields_ = [("Lx", ctypes.c_int32), ("Ly", ctypes.c_int32), ("geometry", ctypes.c_int32),
                 ("boundary", ctypes.c_int32), ("packing", ctypes.c_int32),
-                ("cluster", ctypes.c_int32), ("n_A", ctypes.c_int64),
+                ("cluster", ctypes.c_int32), ("threads", ctypes.c_int32),
+                ("reserved0", ctypes.c_int32), ("n_A", ctypes.c_int64),
                 ("fraction_A", ctypes.c_double), ("omega_over_kT", ctypes.c_double),
                 ("seed", ctypes.c_uint64), ("alloc", ALLOC_FN), ("free", FREE_FN),
                 ("user", ctypes.c_void_p), ("stream", ctypes.c_void_p)]
@@ -119,6 +120,7 @@ def lib():
         "klmc_batch_create": [P(vp), P(Params), i32],
         "klmc_batch_sweep": [vp, P(i64)],
         "klmc_batch_replica": [vp, i32, P(vp)],
+        "klmc_batch_get_launch": [vp, i32, P(i32), P(i32)],
         "klmc_batch_destroy": [vp],
         "klmc_server_create": [P(vp), ctypes.c_size_t, vp],
         "klmc_server_submit": [vp, P(Params), i64, i64, ctypes.c_uint32, P(u64)],
@@ -180,7 +182,7 @@ class _TorchAllocator:
 
 def make_params(Lx: int, Ly: int | None = None, *, geometry: int = TRI6, packing: int = PACK_BIT,
                 n_A: int = -1, fraction_A: float = 0.5, omega_over_kT: float = 0.0, seed: int = 1,
-                cluster: int = 0, stream: int | None = None,
+                cluster: int = 0, threads: int = 0, stream: int | None = None,
                 allocator: _TorchAllocator | None = None) -> Params:
     p = Params()
     _check(lib().klmc_params_default(ctypes.byref(p)))
@@ -193,6 +195,7 @@ def make_params(Lx: int, Ly: int | None = None, *, geometry: int = TRI6, packing
     p.omega_over_kT = float(omega_over_kT)
     p.seed = int(seed)
     p.cluster = int(cluster)
+    p.threads = int(threads)
     p.stream = stream
     if allocator is not None:
         p.alloc = allocator.alloc
@@ -205,8 +208,8 @@ class Lattice:
 
     def __init__(self, Lx: int, Ly: int | None = None, *, geometry: int = TRI6,
                  packing: int = PACK_BIT, n_A: int = -1, fraction_A: float = 0.5,
-                 omega_over_kT: float = 0.0, seed: int = 1, cluster: int = 0, stream=None,
-                 torch_allocator: bool = True, _handle=None, _owner=None):
+                 omega_over_kT: float = 0.0, seed: int = 1, cluster: int = 0, threads: int = 0,
+                 stream=None, torch_allocator: bool = True, _handle=None, _owner=None):
         import torch
 
         self._owner = _owner
@@ -218,7 +221,7 @@ class Lattice:
             self._alloc = _TorchAllocator(dev) if torch_allocator else None
             p = make_params(Lx, Ly, geometry=geometry, packing=packing, n_A=n_A,
                             fraction_A=fraction_A, omega_over_kT=omega_over_kT, seed=seed,
-                            cluster=cluster, stream=_torch_stream_handle(stream),
+                            cluster=cluster, threads=threads, stream=_torch_stream_handle(stream),
                             allocator=self._alloc)
             h = ctypes.c_void_p()
             _check(lib().klmc_create_ex(ctypes.byref(h), ctypes.byref(p)))
@@ -356,6 +359,12 @@ class Batch:
             n_mcs = [int(n_mcs)] * self.n
         arr = (ctypes.c_int64 * self.n)(*[int(v) for v in n_mcs])
         _check(lib().klmc_batch_sweep(self._h, arr))
+
+    def launch_shape(self, i: int) -> tuple[int, int]:
+        """(CTAs per replica, threads per CTA) replica i ran with in the last sweep."""
+        c, t = ctypes.c_int32(), ctypes.c_int32()
+        _check(lib().klmc_batch_get_launch(self._h, int(i), ctypes.byref(c), ctypes.byref(t)))
+        return c.value, t.value
 
     def close(self):
         if getattr(self, "_h", None):

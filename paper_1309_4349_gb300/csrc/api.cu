@@ -110,6 +110,10 @@ klmc_status validate(const klmc_params *p)
     if (p->cluster < -1 || p->cluster > 16) return fail(KLMC_EINVAL, "cluster must be in [-1, 16]");
     if (p->cluster > 1 && p->Ly / p->cluster < 4)
         return fail(KLMC_EINVAL, "cluster too large: every band needs >= 4 rows");
+    if (p->threads != 0 && p->threads != 128 && p->threads != 256 && p->threads != 512)
+        return fail(KLMC_EINVAL, "threads must be 0, 128, 256 or 512");
+    if (p->threads == 512 && p->cluster > 1)
+        return fail(KLMC_EINVAL, "512 threads per CTA only with one CTA per lattice");
     return KLMC_OK;
 }
 
@@ -202,7 +206,13 @@ klmc_status create_one(klmc_ctx **out, const klmc_params *p, klmc_batch *owner, 
         resident_smem_bytes(p->Lx, p->Ly, c->cluster) > (size_t)resident_max_smem_bytes())
         c->cluster = -1;  // automatic choice, too large for shared memory: tiled path
     c->threads = resident_default_threads(c->cluster);
-    if (p->cluster == 0) tuned_shape(p->Lx, p->Ly, p->geometry, c->p.packing, &c->cluster, &c->threads);
+    if (p->cluster == 0 && p->threads == 0)
+        tuned_shape(p->Lx, p->Ly, p->geometry, c->p.packing, &c->cluster, &c->threads);
+    c->auto_shape = p->cluster == 0 && p->threads == 0;
+    if (p->threads != 0) {
+        c->threads = p->threads;
+        if (c->threads == 512 && c->cluster > 1) c->threads = 256;  // automatic cluster > 1
+    }
     if (c->p.packing == KLMC_PACK_BIT) {
         c->pitch = (c->W + 3) / 4 * 4;  // 16-byte rows
         c->lat_bytes = (size_t)c->pitch * 4 * p->Ly;
@@ -448,6 +458,7 @@ klmc_status autotune(klmc_ctx *c, int probe_sweeps)
         if (resident_smem_bytes(c->p.Lx, c->p.Ly, C) > (size_t)resident_max_smem_bytes()) continue;
         if (C == 1) cands.push_back({1, 512});
         cands.push_back({C, 256});
+        cands.push_back({C, 128});
     }
     cands.push_back({-1, 256});
     void *slat = dev_alloc(c, c->lat_bytes);
@@ -490,6 +501,39 @@ klmc_status autotune(klmc_ctx *c, int probe_sweeps)
 }
 
 }  // namespace
+
+void klmc::host::choose_shapes(const std::vector<klmc_ctx *> &cs, const std::vector<int64_t> &steps,
+                               int sm_count, bool keep_longest, std::vector<std::pair<int, int>> *shapes)
+{
+    const size_t n = cs.size();
+    shapes->resize(n);
+    long long ctas = 0;
+    for (size_t i = 0; i < n; ++i) {
+        (*shapes)[i] = {cs[i]->cluster, cs[i]->threads};
+        ctas += cs[i]->cluster > 0 ? cs[i]->cluster : 1;
+    }
+    if (ctas <= sm_count) return;
+    std::vector<double> work(n);
+    std::vector<size_t> order(n);
+    for (size_t i = 0; i < n; ++i) {
+        work[i] = (double)steps[i] * model_mcs_us(cs[i]->p.Lx, cs[i]->p.Ly, cs[i]->cluster, cs[i]->threads);
+        order[i] = i;
+    }
+    std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return work[a] > work[b]; });
+    long long left = keep_longest ? sm_count : 0;
+    for (size_t i : order) {
+        klmc_ctx *c = cs[i];
+        const int own = c->cluster > 0 ? c->cluster : 1;
+        if (own <= left || !c->auto_shape || c->cluster < 1) {
+            if (own <= left) left -= own;
+            continue;
+        }
+        int half = c->cluster > 1 ? c->cluster / 2 : 1;
+        if (resident_smem_bytes(c->p.Lx, c->p.Ly, half) > (size_t)resident_max_smem_bytes())
+            half = c->cluster;
+        (*shapes)[i] = {half, 128};
+    }
+}
 
 klmc_status klmc::host::create_async(klmc_ctx **out, const klmc_params *p)
 {
@@ -773,7 +817,8 @@ klmc_status klmc_batch_create(klmc_batch **out, const klmc_params *reps, int32_t
     b->mem_owner = m;
     b->djobs = (SweepJob *)dev_alloc(m, sizeof(SweepJob) * (size_t)n);
     b->dcalls = (SweepCall *)dev_alloc(m, sizeof(SweepCall) * (size_t)n);
-    if (!b->djobs || !b->dcalls) {
+    b->dmap = (int *)dev_alloc(m, sizeof(int) * (size_t)n);
+    if (!b->djobs || !b->dcalls || !b->dmap) {
         klmc_batch_destroy(b);
         return fail(KLMC_ENOMEM, "device allocation of the batch tables failed");
     }
@@ -787,49 +832,16 @@ klmc_status klmc_batch_create(klmc_batch **out, const klmc_params *reps, int32_t
         return fail(KLMC_ECUDA, std::string("batch upload: ") + cudaGetErrorString(e));
     }
     b->hcalls.resize(n);
-    // Group replicas by cluster size (one launch per group, each on its own stream so
-    // the groups overlap on the GPU); inside a group, larger lattices first.
-    std::map<std::pair<int, int>, std::vector<int>> by_cluster;
-    for (int i = 0; i < n; ++i) by_cluster[{b->reps[i]->cluster, b->reps[i]->threads}].push_back(i);
-    b->dmap = (int *)dev_alloc(m, sizeof(int) * (size_t)n);
-    if (!b->dmap) {
-        klmc_batch_destroy(b);
-        return fail(KLMC_ENOMEM, "device allocation of the batch tables failed");
-    }
-    for (auto it = by_cluster.rbegin(); it != by_cluster.rend(); ++it) {
-        std::vector<int> &idx = it->second;
-        std::stable_sort(idx.begin(), idx.end(), [&](int a, int c) {
-            return b->reps[a]->N > b->reps[c]->N;
-        });
-        klmc_batch::Group g;
-        g.cluster = it->first.first;
-        g.threads = it->first.second;
-        g.offset = (int)b->hmap.size();
-        g.count = (int)idx.size();
-        g.smem = 0;
-        for (int i : idx) {
-            const size_t sm = resident_smem_bytes(b->reps[i]->p.Lx, b->reps[i]->p.Ly, g.cluster);
-            if (sm > g.smem) g.smem = sm;
-        }
-        g.stream = nullptr;
-        g.done = nullptr;
-        if (cudaStreamCreateWithFlags(&g.stream, cudaStreamNonBlocking) != cudaSuccess ||
-            cudaEventCreateWithFlags(&g.done, cudaEventDisableTiming) != cudaSuccess) {
-            b->groups.push_back(g);
-            klmc_batch_destroy(b);
-            return fail(KLMC_ECUDA, "stream/event creation failed");
-        }
-        b->groups.push_back(g);
-        b->hmap.insert(b->hmap.end(), idx.begin(), idx.end());
-    }
+    for (klmc_ctx *c : b->reps) b->last_shape.push_back({c->cluster, c->threads});
     e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(b->dmap, b->hmap.data(), sizeof(int) * (size_t)n, cudaMemcpyHostToDevice,
-                            b->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e == cudaSuccess) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&b->sm_count, cudaDevAttrMultiProcessorCount, dev);
+    }
     if (e != cudaSuccess) {
         klmc_batch_destroy(b);
-        return fail(KLMC_ECUDA, std::string("batch groups: ") + cudaGetErrorString(e));
+        return fail(KLMC_ECUDA, std::string("batch events: ") + cudaGetErrorString(e));
     }
     *out = b;
     return KLMC_OK;
@@ -839,7 +851,9 @@ klmc_status klmc_batch_sweep(klmc_batch *b, const int64_t *n_mcs)
 {
     if (!b || !n_mcs) return fail(KLMC_EINVAL, "NULL argument");
     const int n = (int)b->reps.size();
-    bool any = false;
+    std::vector<klmc_ctx *> active;
+    std::vector<int64_t> active_steps;
+    std::vector<int> index;
     for (int i = 0; i < n; ++i) {
         if (n_mcs[i] < 0) return fail(KLMC_EINVAL, "n_mcs entries must be >= 0");
         klmc_ctx *c = b->reps[i];
@@ -848,25 +862,68 @@ klmc_status klmc_batch_sweep(klmc_batch *b, const int64_t *n_mcs)
         call.n_mcs = n_mcs[i];
         call.trace = nullptr;
         call.trace_every = 0;
-        any = any || n_mcs[i] > 0;
+        if (n_mcs[i] > 0) {
+            active.push_back(c);
+            active_steps.push_back(n_mcs[i]);
+            index.push_back(i);
+        }
     }
-    if (!any) return KLMC_OK;
+    if (active.empty()) return KLMC_OK;
+    // One launch per launch shape, each on its own stream (the launches overlap on
+    // the GPU), larger lattices first inside a launch.
+    std::vector<std::pair<int, int>> shapes;
+    klmc::host::choose_shapes(active, active_steps, b->sm_count, false, &shapes);
+    std::map<std::pair<int, int>, std::vector<int>> groups;
+    for (size_t k = 0; k < active.size(); ++k) {
+        groups[shapes[k]].push_back(index[k]);
+        b->last_shape[index[k]] = shapes[k];
+    }
+    std::vector<int> hmap;
+    hmap.reserve(active.size());
+    for (auto &g : groups) {
+        std::stable_sort(g.second.begin(), g.second.end(),
+                         [&](int a, int c) { return b->reps[a]->N > b->reps[c]->N; });
+        hmap.insert(hmap.end(), g.second.begin(), g.second.end());
+    }
     KLMC_CUDA(cudaMemcpyAsync(b->dcalls, b->hcalls.data(), sizeof(SweepCall) * (size_t)n,
                               cudaMemcpyHostToDevice, b->stream));
-    // Fork: every group stream waits for the call table; join: the batch stream
-    // waits for every group.
+    KLMC_CUDA(cudaMemcpyAsync(b->dmap, hmap.data(), sizeof(int) * hmap.size(), cudaMemcpyHostToDevice,
+                              b->stream));
     KLMC_CUDA(cudaEventRecord(b->fork, b->stream));
-    for (auto &g : b->groups) {
-        bool group_active = false;
-        for (int k = 0; k < g.count; ++k) group_active = group_active || n_mcs[b->hmap[g.offset + k]] > 0;
-        if (!group_active) continue;
-        KLMC_CUDA(cudaStreamWaitEvent(g.stream, b->fork, 0));
-        KLMC_CUDA(launch_resident_sweep(b->djobs, b->dcalls, b->dmap + g.offset, g.count, g.cluster,
-                                        g.threads, g.smem, g.stream));
-        KLMC_CUDA(cudaEventRecord(g.done, g.stream));
-        KLMC_CUDA(cudaStreamWaitEvent(b->stream, g.done, 0));
+    int offset = 0;
+    for (auto &g : groups) {
+        auto it = b->group_streams.find(g.first);
+        if (it == b->group_streams.end()) {
+            cudaStream_t gs;
+            cudaEvent_t ge;
+            KLMC_CUDA(cudaStreamCreateWithFlags(&gs, cudaStreamNonBlocking));
+            KLMC_CUDA(cudaEventCreateWithFlags(&ge, cudaEventDisableTiming));
+            it = b->group_streams.emplace(g.first, std::make_pair(gs, ge)).first;
+        }
+        size_t smem = 0;
+        for (int i : g.second) {
+            klmc_status st = check_resident(b->reps[i], g.first.first);
+            if (st != KLMC_OK) return st;
+            const size_t sm = resident_smem_bytes(b->reps[i]->p.Lx, b->reps[i]->p.Ly, g.first.first);
+            if (sm > smem) smem = sm;
+        }
+        KLMC_CUDA(cudaStreamWaitEvent(it->second.first, b->fork, 0));
+        KLMC_CUDA(launch_resident_sweep(b->djobs, b->dcalls, b->dmap + offset, (int)g.second.size(),
+                                        g.first.first, g.first.second, smem, it->second.first));
+        KLMC_CUDA(cudaEventRecord(it->second.second, it->second.first));
+        KLMC_CUDA(cudaStreamWaitEvent(b->stream, it->second.second, 0));
+        offset += (int)g.second.size();
     }
     for (int i = 0; i < n; ++i) b->reps[i]->sweep += n_mcs[i];
+    return KLMC_OK;
+}
+
+klmc_status klmc_batch_get_launch(klmc_batch *b, int32_t i, int32_t *cluster, int32_t *threads_per_cta)
+{
+    if (!b) return fail(KLMC_EINVAL, "NULL batch");
+    if (i < 0 || i >= (int)b->reps.size()) return fail(KLMC_EINVAL, "replica index out of range");
+    if (cluster) *cluster = b->last_shape[i].first;
+    if (threads_per_cta) *threads_per_cta = b->last_shape[i].second;
     return KLMC_OK;
 }
 
@@ -882,12 +939,10 @@ klmc_status klmc_batch_destroy(klmc_batch *b)
 {
     if (!b) return KLMC_OK;
     if (b->stream) cudaStreamSynchronize(b->stream);
-    for (auto &g : b->groups) {
-        if (g.stream) {
-            cudaStreamSynchronize(g.stream);
-            cudaStreamDestroy(g.stream);
-        }
-        if (g.done) cudaEventDestroy(g.done);
+    for (auto &g : b->group_streams) {
+        cudaStreamSynchronize(g.second.first);
+        cudaStreamDestroy(g.second.first);
+        cudaEventDestroy(g.second.second);
     }
     if (b->fork) cudaEventDestroy(b->fork);
     // The batch tables were allocated on reps[0]; free them with it, last.

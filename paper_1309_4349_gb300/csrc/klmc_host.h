@@ -17,7 +17,8 @@ struct klmc_ctx {
     bool nA_on_device = false;    // nA must be read back from state[kNA]
     int W = 0, pitch = 0;
     int cluster = 1;              // CTAs per lattice in the resident sweep (-1: tiled path)
-    int threads = 512;            // threads per CTA of the resident sweep (512 or 256)
+    int threads = 512;            // threads per CTA of the resident sweep (128, 256 or 512)
+    bool auto_shape = true;       // shape chosen by the library (params cluster = threads = 0)
     size_t lat_bytes = 0;
     void *lat = nullptr;
     long long *state = nullptr;   // StateSlot array
@@ -42,20 +43,15 @@ struct klmc_batch {
     std::vector<klmc_ctx *> reps;
     klmc::SweepJob *djobs = nullptr;
     klmc::SweepCall *dcalls = nullptr;
-    int *dmap = nullptr;            // replica indices grouped by cluster size, largest first
+    int *dmap = nullptr;            // per call: active replicas grouped by launch shape
     std::vector<klmc::SweepCall> hcalls;
     cudaStream_t stream = nullptr;
     klmc_ctx *mem_owner = nullptr;  // holds the batch arrays' allocations
-    // groups of replicas sharing a cluster size: (cluster, offset into dmap, count)
-    struct Group {
-        int cluster, threads, offset, count;
-        size_t smem;
-        cudaStream_t stream;
-        cudaEvent_t done;
-    };
-    std::vector<Group> groups;
-    std::vector<int> hmap;
+    // one internal stream and join event per launch shape (cluster, threads)
+    std::map<std::pair<int, int>, std::pair<cudaStream_t, cudaEvent_t>> group_streams;
     cudaEvent_t fork = nullptr;
+    int sm_count = 152;
+    std::vector<std::pair<int, int>> last_shape;  // launch shape per replica, last call
 };
 
 namespace klmc {
@@ -69,6 +65,28 @@ void destroy(klmc_ctx *c);
 // Device bytes a handle with these parameters holds (lattice, state, placement
 // scratch), for admission control.
 size_t device_bytes(const klmc_params *p);
+
+// Model of one step's time (8 phases) of the resident kernel at a launch shape:
+// 1.3 us per phase plus 1 us per round of anchor words per thread.
+inline double model_mcs_us(int Lx, int Ly, int cluster, int threads)
+{
+    const double words = (double)((Lx + 31) / 32);
+    const double tasks = (Ly / 2.0) * words / (cluster > 0 ? cluster : 1);
+    const double rounds = (double)(long long)((tasks + (threads > 0 ? threads : 256) - 1) /
+                                              (threads > 0 ? threads : 256));
+    return 8.0 * (1.3 + rounds);
+}
+
+// Launch shapes (cluster, threads) for one launch over several resident lattices,
+// lattice i to advance by steps[i].  Lattices with fixed shapes keep them.  While
+// the CTAs of all lattices at their own shapes fit the SMs, every lattice keeps its
+// own (latency) shape.  Otherwise lattices with automatic shapes run with half as
+// many CTAs (when the band still fits shared memory) and 128 threads per CTA, so
+// that several CTAs share an SM: all of them when throughput is the goal (a batch
+// call), or all but those whose remaining work takes longest, which keep their own
+// shapes as long as their CTAs fit the SMs, when latency is (a server round).
+void choose_shapes(const std::vector<klmc_ctx *> &cs, const std::vector<int64_t> &steps,
+                   int sm_count, bool keep_longest, std::vector<std::pair<int, int>> *shapes);
 
 }  // namespace host
 }  // namespace klmc

@@ -87,15 +87,12 @@ namespace {
 
 double seconds(const klmc_server *s) { return std::chrono::duration<double>(Clock::now() - s->t0).count(); }
 
-// Steps per round: about 4 ms of work for every job, from a model of the
-// resident kernel's phase time (1.3 us plus 1 us per round of tasks per thread).
-int64_t quantum(const Job *j)
+// Steps per round: about 4 ms of work for every job at the launch shape it runs
+// with this round.
+int64_t quantum(const Job *j, std::pair<int, int> shape)
 {
     const klmc_ctx *c = j->ctx;
-    const double words = std::ceil(c->p.Lx / 32.0);
-    const double tasks = (c->p.Ly / 2.0) * words / (c->cluster > 0 ? c->cluster : 1);
-    const double rounds = std::ceil(tasks / (c->threads > 0 ? c->threads : 256));
-    const double t_mcs_us = 8.0 * (1.3 + rounds);
+    const double t_mcs_us = klmc::host::model_mcs_us(c->p.Lx, c->p.Ly, shape.first, shape.second);
     int64_t q = (int64_t)(4000.0 / t_mcs_us);
     if (q < 1) q = 1;
     int64_t left = j->n_mcs - j->done;
@@ -235,15 +232,23 @@ klmc_status run_round(klmc_server *s)
     std::vector<klmc::SweepCall> hcalls(n);
     std::vector<int64_t> q(n);
     std::map<std::pair<int, int>, std::vector<int>> groups;
+    std::vector<klmc_ctx *> ctxs(n);
+    std::vector<int64_t> remaining(n);
+    for (int i = 0; i < n; ++i) {
+        ctxs[i] = s->active[i]->ctx;
+        remaining[i] = s->active[i]->n_mcs - s->active[i]->done;
+    }
+    std::vector<std::pair<int, int>> shapes;
+    klmc::host::choose_shapes(ctxs, remaining, s->sm_count, true, &shapes);
     for (int i = 0; i < n; ++i) {
         Job *j = s->active[i];
-        q[i] = quantum(j);
+        q[i] = quantum(j, shapes[i]);
         hjobs[i] = j->ctx->job;
         hcalls[i].sweep0 = j->ctx->sweep;
         hcalls[i].n_mcs = q[i];
         hcalls[i].trace = nullptr;
         hcalls[i].trace_every = 0;
-        groups[{j->ctx->cluster, j->ctx->threads}].push_back(i);
+        groups[shapes[i]].push_back(i);
     }
     std::vector<int> hmap;
     hmap.reserve(n);

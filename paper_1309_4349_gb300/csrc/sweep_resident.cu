@@ -357,8 +357,9 @@ resident_sweep_kernel(const SweepJob *__restrict__ jobs, const SweepCall *__rest
     }
 }
 
-// Two variants: 512 threads (one CTA per SM; single lattices on one CTA) and 256
-// threads with at most 128 registers (two CTAs per SM; clusters and batches).
+// Three variants: 512 threads (one CTA per SM; single lattices on one CTA), 256
+// threads with at most 128 registers (two CTAs per SM) and 128 threads with at
+// most 128 registers (four CTAs per SM; batches of many lattices).
 template <int THREADS, int MINB>
 cudaError_t configure_once()
 {
@@ -398,6 +399,11 @@ cudaError_t launch(const SweepJob *d_jobs, const SweepCall *d_calls, const int *
         if (e != cudaSuccess) return e;
         cfg.blockDim = dim3(512, 1, 1);
         e = cudaLaunchKernelEx(&cfg, resident_sweep_kernel<512, 1>, d_jobs, d_calls, d_map, job0, call0);
+    } else if (threads == 128) {
+        e = configure_once<128, 4>();
+        if (e != cudaSuccess) return e;
+        cfg.blockDim = dim3(128, 1, 1);
+        e = cudaLaunchKernelEx(&cfg, resident_sweep_kernel<128, 4>, d_jobs, d_calls, d_map, job0, call0);
     } else {
         e = configure_once<256, 2>();
         if (e != cudaSuccess) return e;

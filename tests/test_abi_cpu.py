@@ -53,7 +53,8 @@ def test_params_default(L):
 
 
 @pytest.mark.parametrize("field,value", [("Lx", 3), ("Ly", 2), ("geometry", 7), ("packing", 9),
-                                         ("boundary", 1), ("n_A", 64 * 64 + 1),
+                                         ("boundary", 1), ("n_A", 64 * 64 + 1), ("threads", 64),
+                                         ("cluster", 17), ("cluster", -2),
                                          ("omega_over_kT", float("nan")),
                                          ("omega_over_kT", float("inf"))])
 def test_create_rejects_invalid(L, field, value):

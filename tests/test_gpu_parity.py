@@ -21,9 +21,9 @@ GEOMS = [klmc.TRI6, klmc.SQ4]
 PACKS = [klmc.PACK_BIT, klmc.PACK_BYTE]
 
 
-def make(Lx, Ly, nA, bw, seed, geometry=klmc.TRI6, packing=klmc.PACK_BIT, cluster=0):
+def make(Lx, Ly, nA, bw, seed, geometry=klmc.TRI6, packing=klmc.PACK_BIT, cluster=0, threads=0):
     return klmc.Lattice(Lx, Ly, geometry=geometry, packing=packing, n_A=nA, omega_over_kT=bw,
-                        seed=seed, cluster=cluster)
+                        seed=seed, cluster=cluster, threads=threads)
 
 
 def assert_same_run(lat, ref):
@@ -155,7 +155,7 @@ def test_autotune_keeps_trajectory(geometry, Lx, Ly, nA, bw):
     cluster, threads = lat.autotune(4)
     assert (cluster, threads) == lat.launch_shape()
     assert cluster == -1 or cluster in (1, 2, 4, 8, 16)
-    assert threads in (256, 512)
+    assert threads in (128, 256, 512)
     assert np.array_equal(lat.get_lattice(), before)
     assert lat.counters() == cnt
     lat.sweep(9)
@@ -163,6 +163,17 @@ def test_autotune_keeps_trajectory(geometry, Lx, Ly, nA, bw):
     assert_same_run(lat, ref)
     # a new lattice of the same shape picks the tuned shape up
     assert make(Lx, Ly, nA, bw, seed + 1, geometry).launch_shape() == (cluster, threads)
+
+
+@pytest.mark.parametrize("cluster,threads", [(1, 128), (1, 256), (1, 512), (3, 128), (8, 128), (16, 128)])
+def test_thread_variant_parity(cluster, threads):
+    """Every (CTAs per lattice, threads per CTA) variant gives the oracle's trajectory."""
+    Lx, Ly, nA, bw, seed = 131, 100, 3300, 0.9, 61
+    lat = make(Lx, Ly, nA, bw, seed, cluster=cluster, threads=threads)
+    assert lat.launch_shape() == (cluster, threads)
+    lat.sweep(11)
+    ref = oracle.run(Lx, Ly, klmc.TRI6, bw, seed, oracle.init(Lx, Ly, nA, seed), 0, 11)
+    assert_same_run(lat, ref)
 
 
 def test_cluster_size_rejected():
@@ -173,6 +184,10 @@ def test_cluster_size_rejected():
         make(64, 64, 100, 0.5, 1, cluster=17)
     with pytest.raises(klmc.KlmcError):
         make(64, 64, 100, 0.5, 1, cluster=-2)
+    with pytest.raises(klmc.KlmcError):
+        make(64, 64, 100, 0.5, 1, cluster=2, threads=512)
+    with pytest.raises(klmc.KlmcError):
+        make(64, 64, 100, 0.5, 1, threads=64)
 
 
 @pytest.mark.parametrize("geometry", GEOMS)
@@ -311,6 +326,37 @@ def test_batch_parity_mixed():
                          oracle.init(r["Lx"], r["Ly"], r["n_A"], r["seed"]), 0, n + 3)
         assert_same_run(lat, ref)
         assert lat.counters()["sweeps"] == n + 3
+    b.close()
+
+
+def test_batch_oversubscribed_runs_throughput_shape():
+    """More 200 x 200 replicas (8 CTAs each at their own shape) than the GPU's SMs
+    hold: the call runs the replicas with automatic shapes at 4 CTAs of 128
+    threads, a replica with a fixed shape keeps its shape, a call that advances few
+    replicas uses the own shapes again, and every trajectory still equals the
+    oracle's."""
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    n = nsm // 8 + 2
+    reps = [dict(Lx=200, Ly=200, n_A=12000 + 7 * i, omega_over_kT=0.3 + 0.05 * (i % 9), seed=40 + i,
+                 geometry=klmc.SQ4 if i % 5 == 2 else klmc.TRI6) for i in range(n)]
+    reps[3]["cluster"] = 8
+    b = klmc.Batch(reps)
+    own = [r.launch_shape() for r in b.replicas]
+    assert own[0] == (8, 256) and own[3][0] == 8
+    steps = [4 + (i % 3) for i in range(n)]
+    b.sweep(steps)
+    for i in range(n):
+        assert b.launch_shape(i) == (own[i] if i == 3 else (4, 128)), i
+    few = [0] * n
+    few[0], few[3] = 3, 2
+    b.sweep(few)
+    assert b.launch_shape(0) == own[0] and b.launch_shape(3) == own[3]
+    for i in (0, 1, 2, 3, n - 1):
+        r = reps[i]
+        g = r.get("geometry", klmc.TRI6)
+        ref = oracle.run(200, 200, g, r["omega_over_kT"], r["seed"],
+                         oracle.init(200, 200, r["n_A"], r["seed"]), 0, steps[i] + few[i])
+        assert_same_run(b.replicas[i], ref)
     b.close()
 
 
