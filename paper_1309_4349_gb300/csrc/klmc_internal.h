@@ -56,6 +56,9 @@ struct SweepCall {
 // the per-CTA limit, and the largest cluster whose bands keep >= 4 rows.
 size_t resident_smem_bytes(int Lx, int Ly, int cluster);
 int resident_max_smem_bytes();
+// Phases between halo exchanges of a lattice split over `cluster` CTAs (1: a
+// cluster barrier after every phase).
+int resident_block_phases(int Lx, int Ly, int cluster);
 int resident_max_cluster(int Ly);
 int resident_default_threads(int cluster);  // 512 for one CTA, else 256
 

@@ -100,6 +100,67 @@ __device__ void phase_params(int geometry, int Lx, int Ly, int W, int Y0, int Y1
     P->ntask = (P->n1 + P->n2) * W;
 }
 
+// Phase parameters of (sweep s, phase f) and the anchor rows whose row lies in
+// [lo, hi) modulo Ly (hi - lo <= Ly; lo may be negative and hi may exceed Ly).
+// The anchor rows y_m = (ry + py m) mod Ly, m < My, come as up to four runs of
+// consecutive m; task row mi (0 <= mi < c[3]) has m = a[i] + mi for the first run
+// i with mi < c[i].
+struct PhaseR {
+    int oi, rx, ry, px, py, umax;
+    int a[4], c[4];
+    int ntask;
+};
+
+__device__ void phase_ranges(int geometry, int Lx, int Ly, int W, int lo, int hi, uint32_t k0,
+                             uint32_t k1, long long s, int f, PhaseR *P)
+{
+    Philox4 w = philox4(0xFFFFFFFFu, (uint32_t)f, (uint32_t)(unsigned long long)s,
+                        (uint32_t)((unsigned long long)s >> 32), k0, k1);
+    const int nO = geometry == kTRI6 ? 3 : 2;
+    const int oi = (int)__umulhi(w.v[0], (uint32_t)nO);
+    const int rx = (int)__umulhi(w.v[1], (uint32_t)Lx);
+    const int ry = (int)__umulhi(w.v[2], (uint32_t)Ly);
+    int px, py, Kx, My;
+    if (oi == 1) {
+        px = 2; py = 4;
+        Kx = (Lx - 2) / 2 + 1;
+        My = (Ly - 3) / 4 + 1;
+    } else {
+        px = 4; py = 2;
+        Kx = (Lx - 3) / 4 + 1;
+        My = (Ly - 2) / 2 + 1;
+    }
+    const int M1 = min(My, ceil_div(Ly - ry, py));  // m < M1: y_m = ry + py m (no wrap)
+    // [lo, hi) as at most two intervals of [0, Ly)
+    int u[2], v[2];
+    if (lo < 0) {
+        u[0] = lo + Ly; v[0] = Ly; u[1] = 0; v[1] = hi;
+    } else if (hi > Ly) {
+        u[0] = lo; v[0] = Ly; u[1] = 0; v[1] = hi - Ly;
+    } else {
+        u[0] = lo; v[0] = hi; u[1] = 0; v[1] = 0;
+    }
+    int total = 0;
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+#pragma unroll
+        for (int wr = 0; wr < 2; ++wr) {
+            const int off = wr ? Ly : 0;
+            int a = ceil_div(u[q] + off - ry, py);
+            int b = floor_div(v[q] - 1 + off - ry, py);
+            a = max(a, wr ? M1 : 0);
+            b = min(b, wr ? My - 1 : M1 - 1);
+            const int n = u[q] < v[q] ? max(0, b - a + 1) : 0;
+            P->a[2 * q + wr] = a - total;
+            total += n;
+            P->c[2 * q + wr] = total;
+        }
+    }
+    P->oi = oi; P->rx = rx; P->ry = ry; P->px = px; P->py = py;
+    P->umax = px * (Kx - 1);
+    P->ntask = total * W;
+}
+
 // Bits p of the word at x0 with x0 + p in [lo, hi].
 __device__ __forceinline__ uint32_t range_mask(int lo, int hi, int x0)
 {
@@ -109,7 +170,8 @@ __device__ __forceinline__ uint32_t range_mask(int lo, int hi, int x0)
 }
 
 // Anchors of the phase in the word at x0: x = (rx + px k) mod Lx, k < Kx.
-__device__ __forceinline__ uint32_t anchor_mask(int x0, const PhaseP &P, int Lx)
+template <typename PP>
+__device__ __forceinline__ uint32_t anchor_mask(int x0, const PP &P, int Lx)
 {
     const uint32_t rep = P.px == 4 ? 0x11111111u : 0x55555555u;
     const int pm = P.px - 1;

@@ -13,6 +13,19 @@
 // neighbouring CTAs, through distributed shared memory.  Phases are separated by
 // a cluster barrier (release/acquire), so the next phase sees every flip.
 //
+// Phase blocks.  When the bands are tall enough, a cluster of C > 1 CTAs instead
+// advances K consecutive phases (K = 2, 4 or 8) between exchanges.  Each CTA
+// keeps D = 2K + 1 halo rows on each side, and in the j-th phase of a block
+// evaluates every anchor within 2 (K - 1 - j) + 1 rows of its band: a site's new
+// value depends only on sites at most two rows away, so after K phases the band
+// is exact although the outer halo rows are not.  The anchors outside the band
+// are evaluated again by the CTA that owns them, with the same counter-based
+// random numbers, hence identical results; only anchors of the own band are
+// counted.  All flips are local.  At the end of a block each CTA stores its D
+// lowest and D highest band rows into mailboxes in the neighbouring CTAs'
+// shared memory (double-buffered by block parity), one cluster barrier follows,
+// and each CTA copies its mailboxes into its halo rows.
+//
 // Row layout.  A shared-memory row is RW 32-bit words holding the padded bit
 // positions pos in [-32, 32*RW - 32); when loaded, position pos holds site
 // (pos mod Lx), so the 32-site window starting at any x in [-32, Lx + 32] is one
@@ -85,6 +98,8 @@ struct Geo {
     int prevY, prevH;    // band of CTA rank-1 (mod C)
     int nextY, nextH;    // band of CTA rank+1 (mod C)
     uint32_t lat_addr;   // shared address of local row 0
+    int D;               // halo rows on each side: local row lr holds row (Y0 - D + lr) mod Ly
+    int base;            // (Y0 - D) mod Ly
 };
 
 // Flip, in one copy of a row, the sites x0 + i (bit i of m, x0 = 32 j, every site
@@ -140,9 +155,12 @@ __device__ __forceinline__ void phase_barrier(int C)
     }
 }
 
-// One phase of one band.  Every task is (anchor row, word j).
-template <int G, int OI, int THREADS>
-__device__ __forceinline__ void run_phase(const uint32_t *lat, const Geo &g, const PhaseP &P,
+// One phase of one band.  Every task is (anchor row, word j).  BLOCKED: the
+// anchors span the band and part of its halo, all flips are local, and only
+// anchors of the band are counted; otherwise the anchors are those of the band
+// and flips reach every copy of their rows.
+template <int G, int OI, int THREADS, bool BLOCKED>
+__device__ __forceinline__ void run_phase(const uint32_t *lat, const Geo &g, const PhaseR &P,
                                           const uint64_t *thr, int f,
                                           uint32_t s_lo, uint32_t s_hi, Acc &A)
 {
@@ -150,20 +168,28 @@ __device__ __forceinline__ void run_phase(const uint32_t *lat, const Geo &g, con
     constexpr int bdy = OI == 0 ? 0 : (OI == 1 ? 1 : -1);
     constexpr int bdx = OI == 1 ? 0 : 1;
     const int lane = threadIdx.x & 31;
+    const int H = g.Y1 - g.Y0;
     for (int t0 = threadIdx.x & ~31; t0 < P.ntask; t0 += THREADS) {
         const int t = t0 + lane;
         uint32_t am = 0u, ta = 0u, tb = 0u;
         Planes S = {0u, 0u, 0u, 0u};
-        int y = 0, x0 = 0;
+        int y = 0, x0 = 0, lr = 0;
         if (t < P.ntask) {
             const int mi = (int)(((unsigned long long)t * g.magicW) >> 32);
             const int j = t - mi * g.W;
-            const int m = mi < P.n1 ? P.a1 + mi : P.a2 + (mi - P.n1);
+            const int m = mi < P.c[0] ? P.a[0] + mi
+                        : (mi < P.c[1] ? P.a[1] + mi : (mi < P.c[2] ? P.a[2] + mi : P.a[3] + mi));
             y = P.ry + P.py * m;
             if (y >= g.Ly) y -= g.Ly;
+            if (BLOCKED) {
+                lr = y - g.base;
+                if (lr < 0) lr += g.Ly;
+            } else {
+                lr = y - g.Y0 + 2;  // y is a band row
+            }
             x0 = j << 5;
             am = anchor_mask(x0, P, g.Lx);
-            evaluate<G, OI>(lat + (size_t)(y - g.Y0 + 2) * g.RW, g.RW, j, ta, tb, S);
+            evaluate<G, OI>(lat + (size_t)lr * g.RW, g.RW, j, ta, tb, S);
         }
         const uint32_t unl = (ta ^ tb) & am;
         const uint32_t dmask = unl & draw_positions<G>(S, g.sign);
@@ -171,17 +197,20 @@ __device__ __forceinline__ void run_phase(const uint32_t *lat, const Geo &g, con
 
         acc |= draw_accepts(dmask, S, (uint32_t)(y * g.Lx + x0), (uint32_t)f, s_lo, s_hi, g.k0,
                             g.k1, thr);
-        const int nd = __popc(dmask);
-
-        A.att += __popc(am);
-        A.unl += __popc(unl);
-        A.drw += nd;
+        const bool own = !BLOCKED || (unsigned)(lr - g.D) < (unsigned)H;
+        if (own) {
+            A.att += __popc(am);
+            A.unl += __popc(unl);
+            A.drw += __popc(dmask);
+        }
         if (acc) {
-            const int na = __popc(acc);
-            A.acc += na;
-            const int sum_s = __popc(S.s0 & acc) + 2 * __popc(S.s1 & acc) +
-                              4 * __popc(S.s2 & acc) + 8 * __popc(S.s3 & acc);
-            A.dn += 2 * (sum_s - g.zm1 * na);
+            if (own) {
+                const int na = __popc(acc);
+                A.acc += na;
+                const int sum_s = __popc(S.s0 & acc) + 2 * __popc(S.s1 & acc) +
+                                  4 * __popc(S.s2 & acc) + 8 * __popc(S.s3 & acc);
+                A.dn += 2 * (sum_s - g.zm1 * na);
+            }
             const int j = x0 >> 5;
             // b sites; with bdx = 1 the pair of anchor Lx-1 wraps to site 0.
             unsigned long long mb = (unsigned long long)acc << bdx;
@@ -193,15 +222,39 @@ __device__ __forceinline__ void run_phase(const uint32_t *lat, const Geo &g, con
                     wrap0 = true;
                 }
             }
-            if (bdy == 0) {
-                flip_global_row(g, y, j, (unsigned long long)acc | mb);
+            if (BLOCKED) {
+                const uint32_t rowbytes = 4u * (uint32_t)g.RW;
+                const uint32_t ra = g.lat_addr + rowbytes * (uint32_t)lr;
+                const uint32_t rb = g.lat_addr + rowbytes * (uint32_t)(lr + bdy);
+                if (bdy == 0) {
+                    flip_row(g, ra, j, (unsigned long long)acc | mb, 0u, true);
+                } else {
+                    flip_row(g, ra, j, (unsigned long long)acc, 0u, true);
+                    flip_row(g, rb, j, mb, 0u, true);
+                }
+                if (wrap0) flip_row(g, rb, 0, 1ull, 0u, true);
             } else {
-                flip_global_row(g, y, j, (unsigned long long)acc);
-                flip_global_row(g, y + bdy, j, mb);
+                const int yu = lr - g.D + g.Y0;  // unwrapped band row
+                if (bdy == 0) {
+                    flip_global_row(g, yu, j, (unsigned long long)acc | mb);
+                } else {
+                    flip_global_row(g, yu, j, (unsigned long long)acc);
+                    flip_global_row(g, yu + bdy, j, mb);
+                }
+                if (wrap0) flip_global_row(g, yu + bdy, 0, 1ull);
             }
-            if (wrap0) flip_global_row(g, y + bdy, 0, 1ull);
         }
     }
+}
+
+template <int G, int THREADS, bool BLOCKED>
+__device__ __forceinline__ void run_phase_oi(const uint32_t *lat, const Geo &g, const PhaseR &P,
+                                             const uint64_t *thr, int f, uint32_t s_lo,
+                                             uint32_t s_hi, Acc &A)
+{
+    if (P.oi == 0) run_phase<G, 0, THREADS, BLOCKED>(lat, g, P, thr, f, s_lo, s_hi, A);
+    else if (G == kTRI6 && P.oi == 2) run_phase<G, 2, THREADS, BLOCKED>(lat, g, P, thr, f, s_lo, s_hi, A);
+    else run_phase<G, 1, THREADS, BLOCKED>(lat, g, P, thr, f, s_lo, s_hi, A);
 }
 
 template <typename T>
@@ -226,6 +279,70 @@ __device__ __forceinline__ uint32_t cluster_ctarank()
     return v;
 }
 
+// Dynamic shared memory a CTA may use (the kernel's static arrays take under 2 KB).
+constexpr int kResidentMaxSmem = 227 * 1024 - 3072;
+
+#ifndef KLMC_MAX_BLOCK
+#define KLMC_MAX_BLOCK 4
+#endif
+
+// Phases per block for a lattice of Lx x Ly sites split over C CTAs: the largest K
+// of 8, 4, 2 (at most KLMC_MAX_BLOCK) whose halo D = 2K + 1 fits in every band
+// (twice, for C = 2, so that a CTA's rows never overlap themselves) and whose
+// rows and mailboxes fit in shared memory; 1 (a cluster barrier per phase)
+// otherwise.
+__host__ __device__ __forceinline__ int block_phases(int Lx, int Ly, int C)
+{
+    if (C <= 1) return 1;
+    const int hmin = Ly / C, hmax = (Ly + C - 1) / C;
+    const long long RW = (Lx + 95) / 32;
+    for (int K = KLMC_MAX_BLOCK; K >= 2; K >>= 1) {
+        const int D = 2 * K + 1;
+        if (D > hmin || (C == 2 && 2 * D > hmin)) continue;
+        if (RW * (hmax + 6 * D) * 4 > kResidentMaxSmem) continue;
+        return K;
+    }
+    return 1;
+}
+
+// Phase table of (sweep s, phase f): the band's anchors, widened for a block.
+__device__ __forceinline__ void phase_table(const SweepJob &J, const Geo &g, int K, long long s, int f,
+                                            PhaseR *P)
+{
+    const int e = K > 1 ? 2 * (K - 1 - f % K) + 1 : 0;
+    phase_ranges(J.geometry, g.Lx, g.Ly, g.W, g.Y0 - e, g.Y1 + e, g.k0, g.k1, s, f, P);
+}
+
+// End of a block: the D lowest and D highest band rows go to the mailboxes of
+// parity p in the neighbouring CTAs, a cluster barrier, then this CTA's own
+// mailboxes of parity p fill its halo rows.
+template <int THREADS>
+__device__ __forceinline__ void exchange_halos(uint32_t *lat, const Geo &g, int hmax, int p)
+{
+    const int H = g.Y1 - g.Y0, D = g.D, rw = D * g.RW;
+    uint32_t *mbox = lat + (size_t)(hmax + 2 * D) * g.RW;
+    const uint32_t prev = g.rank == 0 ? g.C - 1 : g.rank - 1;
+    const uint32_t next = g.rank + 1 == g.C ? 0 : g.rank + 1;
+    for (int idx = threadIdx.x; idx < 2 * rw; idx += THREADS) {
+        const int side = idx >= rw ? 1 : 0;
+        const int k = idx - side * rw;
+        const uint32_t v = lat[(size_t)(side ? D : H) * g.RW + k];
+        const uint32_t local = smem_addr(mbox + (size_t)(2 * p + side) * rw + k);
+        uint32_t remote;
+        asm volatile("mapa.shared::cluster.u32 %0, %1, %2;"
+                     : "=r"(remote) : "r"(local), "r"(side ? prev : next));
+        asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(remote), "r"(v) : "memory");
+    }
+    asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory");
+    asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+    for (int idx = threadIdx.x; idx < 2 * rw; idx += THREADS) {
+        const int side = idx >= rw ? 1 : 0;
+        const int k = idx - side * rw;
+        lat[(size_t)(side ? D + H : 0) * g.RW + k] = mbox[(size_t)(2 * p + side) * rw + k];
+    }
+    __syncthreads();
+}
+
 template <int THREADS, int MINB>
 __global__ void __launch_bounds__(THREADS, MINB)
 resident_sweep_kernel(const SweepJob *__restrict__ jobs, const SweepCall *__restrict__ calls,
@@ -233,7 +350,7 @@ resident_sweep_kernel(const SweepJob *__restrict__ jobs, const SweepCall *__rest
 {
     constexpr int kWarps = THREADS / 32;
     extern __shared__ __align__(16) uint32_t lat[];
-    __shared__ PhaseP pp[2][8];
+    __shared__ PhaseR pp[2][8];
     __shared__ uint64_t thr[16];
     __shared__ long long red[5][kWarps];
 
@@ -262,21 +379,26 @@ resident_sweep_kernel(const SweepJob *__restrict__ jobs, const SweepCall *__rest
         g.nextH = (int)(((long long)(nr + 1) * g.Ly) / C) - g.nextY;
     }
     g.lat_addr = smem_addr(lat);
+    const int K = block_phases(g.Lx, g.Ly, C);
+    const bool blocked = K > 1;
+    g.D = blocked ? 2 * K + 1 : 2;
+    g.base = g.Y0 - g.D < 0 ? g.Y0 - g.D + g.Ly : g.Y0 - g.D;
+    const int hmax = (g.Ly + C - 1) / C;
     const int tid = threadIdx.x;
-    const int NL = g.Y1 - g.Y0 + 4;
+    const int H = g.Y1 - g.Y0;
+    const int NL = H + 2 * g.D;
 
     // Load band and halo rows into padded shared-memory rows.
     for (int idx = tid; idx < NL * g.RW; idx += THREADS) {
         const int lr = idx / g.RW, w = idx - lr * g.RW;
-        int y = g.Y0 - 2 + lr;
+        int y = g.Y0 - g.D + lr;
         y %= g.Ly;
         if (y < 0) y += g.Ly;
         lat[idx] = padded_word(J.lat, J.packing, J.pitch, y, w, g.Lx, g.W);
     }
     if (tid < 16) thr[tid] = J.thr[tid];
-    if (tid < 8)
-        phase_params(J.geometry, g.Lx, g.Ly, g.W, g.Y0, g.Y1, g.k0, g.k1, Cl.sweep0, tid, &pp[0][tid]);
-    // Every CTA of the cluster must be loaded before any peer flips into it.
+    if (tid < 8) phase_table(J, g, K, Cl.sweep0, tid, &pp[0][tid]);
+    // Every CTA of the cluster must be running before any peer writes into it.
     if (C > 1) {
         asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory");
         asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
@@ -288,6 +410,7 @@ resident_sweep_kernel(const SweepJob *__restrict__ jobs, const SweepCall *__rest
     const long long n_unlike0 = (tid == 0 && rank == 0 && Cl.trace_every > 0) ? J.state[kNUnlike] : 0;
     unsigned long long t_att = 0, t_unl = 0, t_drw = 0, t_acc = 0;
     long long t_dn = 0;
+    int block = 0;
     for (long long it = 0; it < Cl.n_mcs; ++it) {
         const long long s = Cl.sweep0 + it;
         const uint32_t s_lo = (uint32_t)(unsigned long long)s;
@@ -295,19 +418,21 @@ resident_sweep_kernel(const SweepJob *__restrict__ jobs, const SweepCall *__rest
         const int buf = (int)(it & 1);
         Acc A = {0u, 0u, 0u, 0u, 0};
         for (int f = 0; f < 8; ++f) {
-            if (f == 7 && tid < 8 && it + 1 < Cl.n_mcs)
-                phase_params(J.geometry, g.Lx, g.Ly, g.W, g.Y0, g.Y1, g.k0, g.k1, s + 1, tid,
-                             &pp[buf ^ 1][tid]);
-            const PhaseP P = pp[buf][f];
-            if (J.geometry == kTRI6) {
-                if (P.oi == 0) run_phase<kTRI6, 0, THREADS>(lat, g, P, thr, f, s_lo, s_hi, A);
-                else if (P.oi == 1) run_phase<kTRI6, 1, THREADS>(lat, g, P, thr, f, s_lo, s_hi, A);
-                else run_phase<kTRI6, 2, THREADS>(lat, g, P, thr, f, s_lo, s_hi, A);
+            if (f == 7 && tid < 8 && it + 1 < Cl.n_mcs) phase_table(J, g, K, s + 1, tid, &pp[buf ^ 1][tid]);
+            const PhaseR P = pp[buf][f];
+            if (blocked) {
+                if (J.geometry == kTRI6) run_phase_oi<kTRI6, THREADS, true>(lat, g, P, thr, f, s_lo, s_hi, A);
+                else run_phase_oi<kSQ4, THREADS, true>(lat, g, P, thr, f, s_lo, s_hi, A);
+                __syncthreads();
+                if (f % K == K - 1 && !(f == 7 && it + 1 == Cl.n_mcs)) {
+                    exchange_halos<THREADS>(lat, g, hmax, block & 1);
+                    ++block;
+                }
             } else {
-                if (P.oi == 0) run_phase<kSQ4, 0, THREADS>(lat, g, P, thr, f, s_lo, s_hi, A);
-                else run_phase<kSQ4, 1, THREADS>(lat, g, P, thr, f, s_lo, s_hi, A);
+                if (J.geometry == kTRI6) run_phase_oi<kTRI6, THREADS, false>(lat, g, P, thr, f, s_lo, s_hi, A);
+                else run_phase_oi<kSQ4, THREADS, false>(lat, g, P, thr, f, s_lo, s_hi, A);
+                phase_barrier(C);
             }
-            phase_barrier(C);
         }
         t_att += A.att; t_unl += A.unl; t_drw += A.drw; t_acc += A.acc;
         t_dn += A.dn;
@@ -325,11 +450,10 @@ resident_sweep_kernel(const SweepJob *__restrict__ jobs, const SweepCall *__rest
     }
 
     // Write the band back (main positions only).
-    const int H = g.Y1 - g.Y0;
     for (int idx = tid; idx < H * g.W; idx += THREADS) {
         const int r = idx / g.W, w = idx - r * g.W;
         const int y = g.Y0 + r;
-        const uint32_t v = lat[(size_t)(r + 2) * g.RW + w + 1];
+        const uint32_t v = lat[(size_t)(r + g.D) * g.RW + w + 1];
         const int pos0 = 32 * w;
         const int nvalid = min(32, g.Lx - pos0);
         if (J.packing == kPackBit) {
@@ -420,20 +544,15 @@ size_t resident_smem_bytes(int Lx, int Ly, int cluster)
 {
     const size_t RW = (size_t)(Lx + 95) / 32;  // ceil(Lx / 32) + 2
     const int C = cluster < 1 ? 1 : cluster;
-    size_t H = 0;  // tallest band
-    for (int c = 0; c < C; ++c) {
-        const size_t h = (size_t)(((long long)(c + 1) * Ly) / C - ((long long)c * Ly) / C);
-        if (h > H) H = h;
-    }
+    const size_t H = (size_t)((Ly + C - 1) / C);  // tallest band
+    const int K = block_phases(Lx, Ly, C);
+    if (K > 1) return RW * (H + 6 * (size_t)(2 * K + 1)) * sizeof(uint32_t);  // rows + mailboxes
     return RW * (H + 4) * sizeof(uint32_t);
 }
 
-int resident_max_smem_bytes()
-{
-    // Dynamic shared memory left after the kernel's static arrays (about 2.2 KB at
-    // 1024 threads: phase tables, thresholds, reductions).
-    return 227 * 1024 - 3072;
-}
+int resident_max_smem_bytes() { return kResidentMaxSmem; }
+
+int resident_block_phases(int Lx, int Ly, int cluster) { return block_phases(Lx, Ly, cluster); }
 
 int resident_default_threads(int cluster) { return cluster == 1 ? 512 : 256; }
 
