@@ -62,8 +62,8 @@ INT32_LANES_PER_SM = 64
 # DRAM bytes (read + write) of one resident-sweep launch of this workload from one ncu
 # capture (profiles/resident_sweep_400x400x5_ncu.md), valid only for the kernel
 # sources it was taken with (hash of sweep_resident.cu + sweep_common.cuh).
-TRAFFIC_C2_LAUNCH = 229888
-TRAFFIC_C2_SOURCES = "137a4d9e64557aa8"
+TRAFFIC_C2_LAUNCH = 209408
+TRAFFIC_C2_SOURCES = "da1cb40eefd0810d"
 
 
 def resident_sources_hash() -> str:

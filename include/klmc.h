@@ -65,7 +65,7 @@ typedef struct klmc_params {
                               (a thread-block cluster, 1..16); -1 = tiled per-phase
                               path; 0 = automatic                                 */
     int32_t threads;       /* threads per CTA of the resident sweep: 128, 256 or
-                              512 (one CTA per lattice only); 0 = automatic        */
+                              512; 0 = automatic                                  */
     int32_t reserved0;
     int64_t n_A;           /* number of A lipids; -1 = floor(fraction_A*N + 0.5)  */
     double fraction_A;     /* used when n_A < 0; in [0, 1]                        */
@@ -193,8 +193,8 @@ klmc_status klmc_set_lattice_device(klmc_ctx *c, const uint8_t *dev_in, int64_t 
 klmc_status klmc_get_shape(klmc_ctx *c, int32_t *Lx, int32_t *Ly, int32_t *geometry, int64_t *n_A);
 
 /* Autotuner: picks the fastest launch shape for this lattice's size by timing
- * every valid shape -- 1, 2, 4, 8 or 16 CTAs per lattice with 512 (one CTA only)
- * or 256 threads per CTA, and the tiled per-phase path -- for probe_sweeps sweeps
+ * every valid shape -- 1, 2, 4, 8 or 16 CTAs per lattice with 512, 256 or 128
+ * threads per CTA, and the tiled per-phase path -- for probe_sweeps sweeps
  * on a scratch copy of the lattice at its current sweep index.  Every candidate's
  * resulting lattice and counters must equal the first candidate's (exactness
  * gate; a differing shape is an error, KLMC_ESTATE).  The choice is cached per
@@ -207,6 +207,13 @@ klmc_status klmc_autotune(klmc_ctx *c, int32_t probe_sweeps, int32_t *cluster, i
  * size, -1 for the tiled per-phase path) and threads per CTA.  Either pointer may
  * be NULL. */
 klmc_status klmc_get_launch(klmc_ctx *c, int32_t *cluster, int32_t *threads_per_cta);
+
+/* Phases a CTA of this handle's resident sweep advances between exchanges of halo
+ * rows with the other CTAs of its lattice: 2, 4 or 8 when the bands are tall
+ * enough for a block (each CTA then re-evaluates 2K+1 halo rows per side); 1 for
+ * a cluster barrier after every phase, for one CTA per lattice, and for the tiled
+ * path.  The trajectory does not depend on it. */
+klmc_status klmc_get_plan(klmc_ctx *c, int32_t *phases_per_exchange);
 
 /* Waits for all work enqueued on the handle's stream. */
 klmc_status klmc_synchronize(klmc_ctx *c);

@@ -121,6 +121,7 @@ def lib():
         "klmc_batch_sweep": [vp, P(i64)],
         "klmc_batch_replica": [vp, i32, P(vp)],
         "klmc_batch_get_launch": [vp, i32, P(i32), P(i32)],
+        "klmc_get_plan": [vp, P(i32)],
         "klmc_batch_destroy": [vp],
         "klmc_server_create": [P(vp), ctypes.c_size_t, vp],
         "klmc_server_submit": [vp, P(Params), i64, i64, ctypes.c_uint32, P(u64)],
@@ -314,6 +315,12 @@ class Lattice:
         c, t = ctypes.c_int32(), ctypes.c_int32()
         _check(lib().klmc_get_launch(self._h, ctypes.byref(c), ctypes.byref(t)))
         return c.value, t.value
+
+    def plan(self) -> int:
+        """Phases advanced between halo exchanges of the resident sweep (1: every phase)."""
+        k = ctypes.c_int32()
+        _check(lib().klmc_get_plan(self._h, ctypes.byref(k)))
+        return k.value
 
     def synchronize(self):
         _check(lib().klmc_synchronize(self._h))

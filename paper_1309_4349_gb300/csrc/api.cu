@@ -112,8 +112,6 @@ klmc_status validate(const klmc_params *p)
         return fail(KLMC_EINVAL, "cluster too large: every band needs >= 4 rows");
     if (p->threads != 0 && p->threads != 128 && p->threads != 256 && p->threads != 512)
         return fail(KLMC_EINVAL, "threads must be 0, 128, 256 or 512");
-    if (p->threads == 512 && p->cluster > 1)
-        return fail(KLMC_EINVAL, "512 threads per CTA only with one CTA per lattice");
     return KLMC_OK;
 }
 
@@ -209,10 +207,7 @@ klmc_status create_one(klmc_ctx **out, const klmc_params *p, klmc_batch *owner, 
     if (p->cluster == 0 && p->threads == 0)
         tuned_shape(p->Lx, p->Ly, p->geometry, c->p.packing, &c->cluster, &c->threads);
     c->auto_shape = p->cluster == 0 && p->threads == 0;
-    if (p->threads != 0) {
-        c->threads = p->threads;
-        if (c->threads == 512 && c->cluster > 1) c->threads = 256;  // automatic cluster > 1
-    }
+    if (p->threads != 0) c->threads = p->threads;
     if (c->p.packing == KLMC_PACK_BIT) {
         c->pitch = (c->W + 3) / 4 * 4;  // 16-byte rows
         c->lat_bytes = (size_t)c->pitch * 4 * p->Ly;
@@ -456,7 +451,7 @@ klmc_status autotune(klmc_ctx *c, int probe_sweeps)
     for (int C : {1, 2, 4, 8, 16}) {
         if (C > 1 && c->p.Ly / C < 4) continue;
         if (resident_smem_bytes(c->p.Lx, c->p.Ly, C) > (size_t)resident_max_smem_bytes()) continue;
-        if (C == 1) cands.push_back({1, 512});
+        cands.push_back({C, 512});
         cands.push_back({C, 256});
         cands.push_back({C, 128});
     }
@@ -769,6 +764,13 @@ klmc_status klmc_get_launch(klmc_ctx *c, int32_t *cluster, int32_t *threads_per_
     if (!c) return fail(KLMC_EINVAL, "ctx is NULL");
     if (cluster) *cluster = c->cluster;
     if (threads_per_cta) *threads_per_cta = c->threads;
+    return KLMC_OK;
+}
+
+klmc_status klmc_get_plan(klmc_ctx *c, int32_t *phases_per_exchange)
+{
+    if (!c || !phases_per_exchange) return fail(KLMC_EINVAL, "NULL argument");
+    *phases_per_exchange = c->cluster > 0 ? resident_block_phases(c->p.Lx, c->p.Ly, c->cluster) : 1;
     return KLMC_OK;
 }
 

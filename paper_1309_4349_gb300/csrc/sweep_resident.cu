@@ -169,12 +169,19 @@ __device__ __forceinline__ void run_phase(const uint32_t *lat, const Geo &g, con
     constexpr int bdx = OI == 1 ? 0 : 1;
     const int lane = threadIdx.x & 31;
     const int H = g.Y1 - g.Y0;
-    for (int t0 = threadIdx.x & ~31; t0 < P.ntask; t0 += THREADS) {
-        const int t = t0 + lane;
+    // Split each word over 2^ls lanes when the phase has that few words: every lane
+    // evaluates the word and keeps the anchors of its part, which divides the draws
+    // (the longest step of a lane) among the lanes.
+    // (At 512 threads the extra evaluations cost more issue slots than they save.)
+    const int ls = THREADS > 256 ? 0 : (4 * P.ntask <= THREADS ? 2 : (2 * P.ntask <= THREADS ? 1 : 0));
+    const int nlane = P.ntask << ls;
+    for (int t0 = threadIdx.x & ~31; t0 < nlane; t0 += THREADS) {
+        const int tl = t0 + lane;
         uint32_t am = 0u, ta = 0u, tb = 0u;
         Planes S = {0u, 0u, 0u, 0u};
         int y = 0, x0 = 0, lr = 0;
-        if (t < P.ntask) {
+        if (tl < nlane) {
+            const int t = tl >> ls;
             const int mi = (int)(((unsigned long long)t * g.magicW) >> 32);
             const int j = t - mi * g.W;
             const int m = mi < P.c[0] ? P.a[0] + mi
@@ -189,6 +196,10 @@ __device__ __forceinline__ void run_phase(const uint32_t *lat, const Geo &g, con
             }
             x0 = j << 5;
             am = anchor_mask(x0, P, g.Lx);
+            if (ls != 0) {
+                const int part = tl & ((1 << ls) - 1), bits = 32 >> ls;
+                am &= (0xFFFFFFFFu >> (32 - bits)) << (part * bits);
+            }
             evaluate<G, OI>(lat + (size_t)lr * g.RW, g.RW, j, ta, tb, S);
         }
         const uint32_t unl = (ta ^ tb) & am;

@@ -176,6 +176,34 @@ def test_thread_variant_parity(cluster, threads):
     assert_same_run(lat, ref)
 
 
+# (Lx, Ly, CTAs, threads, phases between exchanges): blocks of 4 and 2 phases,
+# two-CTA clusters (both neighbours are the same CTA), 512-thread CTAs in a
+# cluster, and a cluster barrier after every phase for bands too thin for a block.
+PLANS = [
+    (131, 100, 8, 128, 4), (131, 100, 3, 512, 4), (400, 400, 16, 512, 4), (400, 400, 16, 256, 4),
+    (37, 29, 2, 128, 2), (45, 23, 2, 512, 2), (2000, 96, 16, 128, 2), (1500, 24, 2, 128, 2),
+    (64, 64, 16, 256, 1), (300, 41, 4, 512, 4),
+]
+
+
+@pytest.mark.parametrize("geometry", GEOMS)
+@pytest.mark.parametrize("Lx,Ly,cluster,threads,K", PLANS)
+def test_plan_parity(geometry, Lx, Ly, cluster, threads, K):
+    """Each plan gives the oracle's trajectory over 9 sweeps in two calls (blocks
+    cross sweep and call boundaries), for omega > 0, < 0 and = 0."""
+    for i, bw in enumerate((0.85, -0.6, 0.0)):
+        seed = 500 + Lx + 7 * i
+        nA = (Lx * Ly * (3 + i)) // 10
+        packing = klmc.PACK_BYTE if (i == 2 and Lx < 200) else klmc.PACK_BIT
+        lat = make(Lx, Ly, nA, bw, seed, geometry, cluster=cluster, threads=threads, packing=packing)
+        assert lat.plan() == K
+        lat.sweep(4)
+        lat.sweep(5)
+        ref = oracle.run(Lx, Ly, geometry, bw, seed, oracle.init(Lx, Ly, nA, seed), 0, 9)
+        assert_same_run(lat, ref)
+        lat.close()
+
+
 def test_cluster_size_rejected():
     with pytest.raises(klmc.KlmcError) as e:
         make(16, 16, 100, 0.5, 1, cluster=8)  # bands of 2 rows
@@ -184,8 +212,6 @@ def test_cluster_size_rejected():
         make(64, 64, 100, 0.5, 1, cluster=17)
     with pytest.raises(klmc.KlmcError):
         make(64, 64, 100, 0.5, 1, cluster=-2)
-    with pytest.raises(klmc.KlmcError):
-        make(64, 64, 100, 0.5, 1, cluster=2, threads=512)
     with pytest.raises(klmc.KlmcError):
         make(64, 64, 100, 0.5, 1, threads=64)
 
