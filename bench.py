@@ -532,15 +532,18 @@ def main():
     init_host = [batch.replicas[i].get_lattice() for i in range(nrun)]
     init_dev = [torch.from_numpy(t).cuda() for t in init_host]
     hcap = int(np.sqrt(2.0 * N)) + 2
-    sizes = torch.zeros((nrun, n_seg, hcap), dtype=torch.int64, device="cuda")
+    sizes = torch.zeros((n_seg, nrun, hcap), dtype=torch.int64, device="cuda")
     counts = torch.zeros_like(sizes)
-    ndist = torch.zeros((nrun, n_seg), dtype=torch.int64, device="cuda")
+    ndist = torch.zeros((n_seg, nrun), dtype=torch.int64, device="cuda")
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
     sweep_events = []
 
     def histograms(lats, seg):
         for i, lat in enumerate(lats):
-            lat.cluster_histogram_device(1, sizes[i, seg], counts[i, seg], ndist[i, seg:seg + 1])
+            lat.cluster_histogram_device(1, sizes[seg, i], counts[seg, i], ndist[seg, i:i + 1])
+
+    def histograms_batched(seg):  # the replicas' histograms overlap on internal streams
+        batch.cluster_histogram_device(1, sizes[seg], counts[seg], ndist[seg])
 
     def step_batched(record=False):
         for i, lat in enumerate(batch.replicas):
@@ -554,7 +557,7 @@ def main():
             if record:
                 e1.record(stream)
                 sweep_events.append((e0, e1))
-            histograms(batch.replicas, seg)
+            histograms_batched(seg)
 
     plain = [batch.replicas[i] for i in range(nrun)]
 
@@ -654,7 +657,7 @@ def main():
             lat.set_lattice(pinned_np[i], 0)
         for seg in range(n_seg):
             batch.sweep(HIST_EVERY)
-            histograms(batch.replicas, seg)
+            histograms_batched(seg)
         h = (sizes.cpu(), counts.cpu(), ndist.cpu())
         energies = [lat.energy()[0] for lat in batch.replicas]
         for i, lat in enumerate(batch.replicas):

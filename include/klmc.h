@@ -239,6 +239,17 @@ klmc_status klmc_batch_create(klmc_batch **out, const klmc_params *reps, int32_t
 /* Enqueues n_mcs[i] steps for replica i (entries may differ; 0 skips). */
 klmc_status klmc_batch_sweep(klmc_batch *b, const int64_t *n_mcs);
 
+/* Cluster-size histograms of the given species for every replica, as
+ * klmc_cluster_histogram_device on each, enqueued on internal streams forked from
+ * and joined back to the batch stream so that the replicas' histograms overlap.
+ * Replica i writes dev_sizes[i*capacity ...], dev_counts[i*capacity ...] (device
+ * int64 arrays of n*capacity) and dev_n_distinct[i] (device int64 array of n);
+ * only the first min(capacity, n_distinct) pairs are written.  Does not
+ * synchronise. */
+klmc_status klmc_batch_cluster_histogram_device(klmc_batch *b, int32_t species, int64_t *dev_sizes,
+                                                int64_t *dev_counts, int64_t capacity,
+                                                int64_t *dev_n_distinct);
+
 /* Launch shape (CTAs per replica, threads per CTA) replica i ran with in the last
  * klmc_batch_sweep that advanced it; before that, the replica's own shape.  Either
  * pointer may be NULL.  EINVAL for an index out of range. */

@@ -121,6 +121,7 @@ def lib():
         "klmc_batch_sweep": [vp, P(i64)],
         "klmc_batch_replica": [vp, i32, P(vp)],
         "klmc_batch_get_launch": [vp, i32, P(i32), P(i32)],
+        "klmc_batch_cluster_histogram_device": [vp, i32, vp, vp, i64, vp],
         "klmc_get_plan": [vp, P(i32)],
         "klmc_batch_destroy": [vp],
         "klmc_server_create": [P(vp), ctypes.c_size_t, vp],
@@ -366,6 +367,17 @@ class Batch:
             n_mcs = [int(n_mcs)] * self.n
         arr = (ctypes.c_int64 * self.n)(*[int(v) for v in n_mcs])
         _check(lib().klmc_batch_sweep(self._h, arr))
+
+    def cluster_histogram_device(self, species: int, sizes, counts, n_distinct):
+        """Every replica's histogram into torch int64 CUDA tensors: sizes and counts of
+        shape (n, capacity), n_distinct of shape (n,); enqueued, not synchronised."""
+        cap = int(sizes.shape[-1]) if sizes is not None else 0
+        for t in (sizes, counts, n_distinct):
+            if t is not None and not t.is_contiguous():
+                raise ValueError("output tensors must be contiguous")
+        _check(lib().klmc_batch_cluster_histogram_device(
+            self._h, int(species), sizes.data_ptr() if sizes is not None else None,
+            counts.data_ptr() if counts is not None else None, cap, n_distinct.data_ptr()))
 
     def launch_shape(self, i: int) -> tuple[int, int]:
         """(CTAs per replica, threads per CTA) replica i ran with in the last sweep."""

@@ -26,6 +26,10 @@ klmc_status fail(klmc_status s, const std::string &msg)
     return s;
 }
 
+// Concurrent streams for a batch's cluster histograms (each histogram is a chain
+// of small launches, latency-bound for the lattice sizes batches hold).
+constexpr int kHistStreams = 8;
+
 #define KLMC_CUDA(expr)                                                                            \
     do {                                                                                           \
         cudaError_t e_ = (expr);                                                                   \
@@ -937,6 +941,44 @@ klmc_status klmc_batch_replica(klmc_batch *b, int32_t i, klmc_ctx **view)
     return KLMC_OK;
 }
 
+klmc_status klmc_batch_cluster_histogram_device(klmc_batch *b, int32_t species, int64_t *dev_sizes,
+                                                int64_t *dev_counts, int64_t capacity,
+                                                int64_t *dev_n_distinct)
+{
+    if (!b || !dev_n_distinct) return fail(KLMC_EINVAL, "NULL argument");
+    if (species != 0 && species != 1) return fail(KLMC_EINVAL, "species must be 0 (B) or 1 (A)");
+    if (capacity < 0 || (capacity > 0 && (!dev_sizes || !dev_counts)))
+        return fail(KLMC_EINVAL, "bad output buffers");
+    const int n = (int)b->reps.size();
+    for (int i = 0; i < n; ++i) {  // scratch first, on the batch stream
+        klmc_status st = ensure_clusters(b->reps[i]);
+        if (st != KLMC_OK) return st;
+    }
+    const int ns = n < kHistStreams ? n : kHistStreams;
+    while ((int)b->hist_streams.size() < ns) {
+        cudaStream_t hs;
+        cudaEvent_t he;
+        KLMC_CUDA(cudaStreamCreateWithFlags(&hs, cudaStreamNonBlocking));
+        KLMC_CUDA(cudaEventCreateWithFlags(&he, cudaEventDisableTiming));
+        b->hist_streams.push_back({hs, he});
+    }
+    KLMC_CUDA(cudaEventRecord(b->fork, b->stream));
+    for (int k = 0; k < ns; ++k) KLMC_CUDA(cudaStreamWaitEvent(b->hist_streams[k].first, b->fork, 0));
+    for (int i = 0; i < n; ++i) {
+        klmc_ctx *c = b->reps[i];
+        const size_t off = (size_t)i * (size_t)capacity;
+        KLMC_CUDA(launch_cluster_histogram(c->lat, c->job.packing, c->p.Lx, c->p.Ly, c->pitch, c->p.geometry,
+                                           species, c->cs, capacity ? (long long *)dev_sizes + off : nullptr,
+                                           capacity ? (long long *)dev_counts + off : nullptr, capacity,
+                                           (long long *)dev_n_distinct + i, b->hist_streams[i % ns].first));
+    }
+    for (int k = 0; k < ns; ++k) {
+        KLMC_CUDA(cudaEventRecord(b->hist_streams[k].second, b->hist_streams[k].first));
+        KLMC_CUDA(cudaStreamWaitEvent(b->stream, b->hist_streams[k].second, 0));
+    }
+    return KLMC_OK;
+}
+
 klmc_status klmc_batch_destroy(klmc_batch *b)
 {
     if (!b) return KLMC_OK;
@@ -945,6 +987,11 @@ klmc_status klmc_batch_destroy(klmc_batch *b)
         cudaStreamSynchronize(g.second.first);
         cudaStreamDestroy(g.second.first);
         cudaEventDestroy(g.second.second);
+    }
+    for (auto &h : b->hist_streams) {
+        cudaStreamSynchronize(h.first);
+        cudaStreamDestroy(h.first);
+        cudaEventDestroy(h.second);
     }
     if (b->fork) cudaEventDestroy(b->fork);
     // The batch tables were allocated on reps[0]; free them with it, last.

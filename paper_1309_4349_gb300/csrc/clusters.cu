@@ -28,21 +28,28 @@ __device__ __forceinline__ uint32_t site_at(const void *lat, int packing, int pi
     return ((const uint8_t *)lat)[(size_t)y * pitch + x] ? 1u : 0u;
 }
 
-__device__ __forceinline__ int find_root(const volatile int32_t *parent, int x)
+// Root of x, shortening the path on the way: every visited node is re-pointed to
+// its grandparent (pointer jumping).  That write is always an ancestor, and only
+// non-roots are written, so it is safe next to the compare-and-swap on roots.
+__device__ __forceinline__ int find_root(volatile int32_t *parent, int x)
 {
     int p = parent[x];
-    while (p != x) {
-        x = p;
-        p = parent[x];
+    if (p == x) return x;
+    int prev = x;
+    int next;
+    while (p != (next = parent[p])) {
+        parent[prev] = next;
+        prev = p;
+        p = next;
     }
-    return x;
+    return p;
 }
 
 __device__ __forceinline__ void unite(int32_t *parent, int a, int b)
 {
     while (true) {
-        a = find_root(parent, a);
-        b = find_root(parent, b);
+        a = find_root((volatile int32_t *)parent, a);
+        b = find_root((volatile int32_t *)parent, b);
         if (a == b) return;
         if (a < b) {
             const int t = a;
@@ -95,7 +102,7 @@ __global__ void cc_size_kernel(long long N, int32_t *parent, int32_t *csize)
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
          i += (long long)gridDim.x * blockDim.x) {
         if (parent[i] < 0) continue;
-        const int r = find_root(parent, (int)i);
+        const int r = find_root((volatile int32_t *)parent, (int)i);
         parent[i] = r;  // an ancestor: concurrent finds stay valid
         atomicAdd(csize + r, 1);
     }

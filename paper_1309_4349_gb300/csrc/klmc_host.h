@@ -52,6 +52,8 @@ struct klmc_batch {
     cudaEvent_t fork = nullptr;
     int sm_count = 152;
     std::vector<std::pair<int, int>> last_shape;  // launch shape per replica, last call
+    // internal streams and join events for the replicas' cluster histograms
+    std::vector<std::pair<cudaStream_t, cudaEvent_t>> hist_streams;
 };
 
 namespace klmc {

@@ -355,6 +355,40 @@ def test_batch_parity_mixed():
     b.close()
 
 
+def test_batch_histograms_match_oracle():
+    """klmc_batch_cluster_histogram_device: every replica's histogram, computed on
+    concurrent streams into one (n, capacity) buffer, equals the oracle's on the
+    replica's lattice, for both species and both geometries; a capacity below the
+    number of distinct sizes truncates the pairs but reports the full count."""
+    reps = [dict(Lx=64 + 9 * i, Ly=50 + 7 * i, n_A=(64 + 9 * i) * (50 + 7 * i) * (2 + i % 4) // 10,
+                 omega_over_kT=0.4 + 0.2 * (i % 5), seed=900 + i,
+                 geometry=klmc.SQ4 if i % 3 == 1 else klmc.TRI6) for i in range(11)]
+    b = klmc.Batch(reps)
+    b.sweep(30)
+    n, cap = len(reps), 256
+    for species in (1, 0):
+        sizes = torch.full((n, cap), -1, dtype=torch.int64, device="cuda")
+        counts = torch.full((n, cap), -1, dtype=torch.int64, device="cuda")
+        nd = torch.full((n,), -1, dtype=torch.int64, device="cuda")
+        b.cluster_histogram_device(species, sizes, counts, nd)
+        torch.cuda.synchronize()
+        for i, (r, lat) in enumerate(zip(reps, b.replicas)):
+            g = r.get("geometry", klmc.TRI6)
+            rs, rc = oracle.cluster_histogram(r["Lx"], r["Ly"], g, lat.get_lattice(), species)
+            k = int(nd[i].item())
+            assert k == rs.size and k <= cap
+            assert np.array_equal(sizes[i, :k].cpu().numpy(), rs)
+            assert np.array_equal(counts[i, :k].cpu().numpy(), rc)
+    small = torch.zeros((n, 1), dtype=torch.int64, device="cuda")
+    nd = torch.zeros((n,), dtype=torch.int64, device="cuda")
+    b.cluster_histogram_device(1, small, small.clone(), nd)
+    torch.cuda.synchronize()
+    for i, (r, lat) in enumerate(zip(reps, b.replicas)):
+        rs, _ = oracle.cluster_histogram(r["Lx"], r["Ly"], r.get("geometry", klmc.TRI6), lat.get_lattice(), 1)
+        assert int(nd[i].item()) == rs.size and int(small[i, 0].item()) == rs[0]
+    b.close()
+
+
 def test_batch_oversubscribed_runs_throughput_shape():
     """More 200 x 200 replicas (8 CTAs each at their own shape) than the GPU's SMs
     hold: the call runs the replicas with automatic shapes at 4 CTAs of 128
