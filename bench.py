@@ -416,10 +416,14 @@ def bench_other(args, klmc, torch, np):
             cnt = lat.counters()
             ms_step = sum(ms) / len(ms)
             attempts = cnt["attempts"]
-            launch_ms = ms_step / (8 * c["mcs"])  # per phase launch, graph gaps included
-            rl = _roofline("tiled_phase_kernel", launch_ms, attempts // (8 * c["mcs"]),
-                           cnt["draws"] / attempts, sm_count, clk["sm_mhz"] if clk else 2070.0,
-                           -1, {"note": "per-launch time = step time / phase launches (graph replays)"})
+            K = lat.plan()  # phases per launch
+            launches = 8 * c["mcs"] // K
+            launch_ms = ms_step / launches  # graph gaps included
+            rl = _roofline("band_phases_kernel" if K > 1 else "tiled_phase_kernel", launch_ms,
+                           attempts // launches, cnt["draws"] / attempts, sm_count,
+                           clk["sm_mhz"] if clk else 2070.0, -1,
+                           {"note": "per-launch time = step time / sweep launches (graph replays)",
+                            "phases_per_launch": K})
             v = {"value": attempts / (ms_step * 1e-3), "ms_per_step": ms_step, "roofline": rl,
                  "clocks": clk, "final_n_unlike": int(trace[-1].item())}
             line["variants"][name] = v
@@ -428,9 +432,10 @@ def bench_other(args, klmc, torch, np):
             lat.close()
         line["config"] = {"workload": "8192x8192 periodic, 50/50 random start, 1 bit/site, omega/kT "
                           "0.85, 1000 MCS, energy trace every 10 MCS (TRI6; SQ4 in variants)",
-                          "form": "tiled per-phase launches replayed from a CUDA graph of 10 MCS",
+                          "form": "tiled path: bands of 54 rows per CTA, 4 phases per launch with "
+                                  "9 halo rows per side, launches replayed from a CUDA graph of 10 MCS",
                           "l2": "lattice (8 MiB) fits L2; flushed between steps"}
-        line["gpu_launches"] = args.steps * (3 + 8 * c["mcs"] + 2 * c["mcs"] // c["trace_every"])
+        line["gpu_launches"] = args.steps * (3 + 8 // K * c["mcs"] + 2 * c["mcs"] // c["trace_every"])
     elif args.workload == "c4":
         reps = c4_replicas()
         b = klmc.Batch([dict(r, packing=klmc.PACK_BIT) for r in reps])

@@ -208,11 +208,13 @@ klmc_status klmc_autotune(klmc_ctx *c, int32_t probe_sweeps, int32_t *cluster, i
  * be NULL. */
 klmc_status klmc_get_launch(klmc_ctx *c, int32_t *cluster, int32_t *threads_per_cta);
 
-/* Phases a CTA of this handle's resident sweep advances between exchanges of halo
- * rows with the other CTAs of its lattice: 2, 4 or 8 when the bands are tall
- * enough for a block (each CTA then re-evaluates 2K+1 halo rows per side); 1 for
- * a cluster barrier after every phase, for one CTA per lattice, and for the tiled
- * path.  The trajectory does not depend on it. */
+/* Phases a CTA of this handle's sweep advances between exchanges of halo rows
+ * with the CTAs of the neighbouring bands: for the resident sweep 2, 4 or 8 when
+ * the bands are tall enough for a block (each CTA then re-evaluates 2K+1 halo
+ * rows per side), 1 for a cluster barrier after every phase and for one CTA per
+ * lattice; for the tiled path the phases per launch (2, 4 or 8 with halo rows read
+ * from the store, 1 for one launch per phase with flips in place).  The
+ * trajectory does not depend on it. */
 klmc_status klmc_get_plan(klmc_ctx *c, int32_t *phases_per_exchange);
 
 /* Waits for all work enqueued on the handle's stream. */

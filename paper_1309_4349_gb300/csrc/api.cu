@@ -274,7 +274,24 @@ klmc_status check_resident(const klmc_ctx *c, int cluster)
     return KLMC_OK;
 }
 
-// Instantiated graph of K sweeps on the tiled path (8 K phase launches, then
+// Tiled-path plan of the handle, and the second store buffer it needs for blocks.
+klmc_status ensure_tiled(klmc_ctx *c)
+{
+    if (c->tiled.H != 0) return KLMC_OK;
+    int dev = 0, sms = 0;
+    KLMC_CUDA(cudaGetDevice(&dev));
+    KLMC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    KLMC_CUDA(configure_tiled());
+    const TiledPlan plan = tiled_plan(c->p.Lx, c->p.Ly, sms);
+    if (plan.K >= 2) {
+        c->tiled_alt = dev_alloc(c, c->lat_bytes);
+        if (!c->tiled_alt) return fail(KLMC_ENOMEM, "device allocation of the tiled path's second buffer failed");
+    }
+    c->tiled = plan;
+    return KLMC_OK;
+}
+
+// Instantiated graph of K sweeps on the tiled path (their phase launches, then
 // state[kSweepBase] += K), built once per handle and K on a private capture stream.
 klmc_status tiled_graph(klmc_ctx *c, int K, cudaGraphExec_t *out)
 {
@@ -287,7 +304,7 @@ klmc_status tiled_graph(klmc_ctx *c, int K, cudaGraphExec_t *out)
         KLMC_CUDA(cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking));
     cudaGraph_t graph = nullptr;
     KLMC_CUDA(cudaStreamBeginCapture(c->capture_stream, cudaStreamCaptureModeThreadLocal));
-    cudaError_t e = launch_tiled_phases(c->job, c->tiled_H, 0, K, c->capture_stream);
+    cudaError_t e = launch_tiled_phases(c->job, c->tiled, c->tiled_alt, c->lat_bytes, 0, K, c->capture_stream);
     if (e == cudaSuccess) e = launch_advance(c->state, K, c->capture_stream);
     cudaError_t e2 = cudaStreamEndCapture(c->capture_stream, &graph);
     if (e == cudaSuccess) e = e2;
@@ -304,13 +321,8 @@ klmc_status tiled_graph(klmc_ctx *c, int K, cudaGraphExec_t *out)
 // the rest, the trace kernel after every trace_every-th sweep.
 klmc_status sweep_tiled(klmc_ctx *c, int64_t n_mcs, int64_t trace_every, int64_t *dev_trace)
 {
-    if (c->tiled_H == 0) {
-        int dev = 0, sms = 0;
-        KLMC_CUDA(cudaGetDevice(&dev));
-        KLMC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-        c->tiled_H = tiled_band_rows(c->p.Ly, sms);
-        KLMC_CUDA(configure_tiled());
-    }
+    klmc_status pst = ensure_tiled(c);
+    if (pst != KLMC_OK) return pst;
     const long long init[3] = {c->sweep, 0, (long long)(intptr_t)dev_trace};
     KLMC_CUDA(cudaMemcpyAsync(c->state + kSweepBase, init, sizeof(init), cudaMemcpyHostToDevice,
                               c->stream));
@@ -328,7 +340,7 @@ klmc_status sweep_tiled(klmc_ctx *c, int64_t n_mcs, int64_t trace_every, int64_t
         }
         if (upto > done) {
             const int r = (int)(upto - done);
-            KLMC_CUDA(launch_tiled_phases(c->job, c->tiled_H, 0, r, c->stream));
+            KLMC_CUDA(launch_tiled_phases(c->job, c->tiled, c->tiled_alt, c->lat_bytes, 0, r, c->stream));
             KLMC_CUDA(launch_advance(c->state, r, c->stream));
             done = upto;
         }
@@ -404,6 +416,10 @@ klmc_status probe_shape(klmc_ctx *c, void *scratch_lat, long long *scratch_state
     SweepJob J = c->job;
     J.lat = scratch_lat;
     J.state = scratch_state;
+    if (cluster < 0) {
+        klmc_status st = ensure_tiled(c);
+        if (st != KLMC_OK) return st;
+    }
     for (int rep = 0; rep < 2; ++rep) {  // the first run warms up; the second is timed
         KLMC_CUDA(cudaMemcpyAsync(scratch_lat, c->lat, c->lat_bytes, cudaMemcpyDeviceToDevice, c->stream));
         KLMC_CUDA(cudaMemcpyAsync(scratch_state, c->state, kStateSlots * sizeof(long long),
@@ -413,11 +429,7 @@ klmc_status probe_shape(klmc_ctx *c, void *scratch_lat, long long *scratch_state
                                   cudaMemcpyHostToDevice, c->stream));
         KLMC_CUDA(cudaEventRecord(e0, c->stream));
         if (cluster < 0) {
-            int dev = 0, sms = 0;
-            KLMC_CUDA(cudaGetDevice(&dev));
-            KLMC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-            KLMC_CUDA(configure_tiled());
-            KLMC_CUDA(launch_tiled_phases(J, tiled_band_rows(c->p.Ly, sms), 0, n, c->stream));
+            KLMC_CUDA(launch_tiled_phases(J, c->tiled, c->tiled_alt, c->lat_bytes, 0, n, c->stream));
             KLMC_CUDA(launch_advance(scratch_state, n, c->stream));
         } else {
             SweepCall call;
@@ -774,7 +786,14 @@ klmc_status klmc_get_launch(klmc_ctx *c, int32_t *cluster, int32_t *threads_per_
 klmc_status klmc_get_plan(klmc_ctx *c, int32_t *phases_per_exchange)
 {
     if (!c || !phases_per_exchange) return fail(KLMC_EINVAL, "NULL argument");
-    *phases_per_exchange = c->cluster > 0 ? resident_block_phases(c->p.Lx, c->p.Ly, c->cluster) : 1;
+    if (c->cluster > 0) {
+        *phases_per_exchange = resident_block_phases(c->p.Lx, c->p.Ly, c->cluster);
+        return KLMC_OK;
+    }
+    int dev = 0, sms = 0;
+    KLMC_CUDA(cudaGetDevice(&dev));
+    KLMC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    *phases_per_exchange = tiled_plan(c->p.Lx, c->p.Ly, sms).K;
     return KLMC_OK;
 }
 

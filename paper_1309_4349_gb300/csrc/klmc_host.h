@@ -34,7 +34,8 @@ struct klmc_ctx {
     klmc_batch *owner = nullptr;  // non-null for replica views
     std::vector<std::pair<void *, size_t>> allocs;
     // tiled path: band height, capture stream, and instantiated graphs of K sweeps
-    int tiled_H = 0;
+    klmc::TiledPlan tiled{0, 0, 0, 0};  // tiled-path plan (H = 0: not yet chosen)
+    void *tiled_alt = nullptr;          // second store buffer of the blocked tiled path
     cudaStream_t capture_stream = nullptr;
     std::map<int, cudaGraphExec_t> graphs;
 };

@@ -73,12 +73,27 @@ cudaError_t launch_resident_sweep(const SweepJob *d_jobs, const SweepCall *d_cal
 cudaError_t launch_resident_sweep_one(const SweepJob &job, const SweepCall &call, int cluster,
                                       int threads, size_t smem_bytes, cudaStream_t stream);
 
-// Tiled path for lattices too large for shared memory: one launch per phase,
-// CTAs of H-row bands (tiled_band_rows), sweep index read from state[kSweepBase].
+// Tiled path for lattices too large for a cluster's shared memory.  Bands of H
+// rows, one CTA each; sweep index read from state[kSweepBase].
+//  K >= 2 (band plan): K phases per launch, each CTA with 2K+1 halo rows read
+//    from one store buffer, its band written to the other (ping-pong).
+//  K = 1: one launch per phase over the store in place, flips by atomics.
+struct TiledPlan {
+    int H, K, threads;
+    size_t smem;
+};
+TiledPlan tiled_plan(int Lx, int Ly, int sm_count);
+// The band plan alone (K = 1 when no block fits shared memory).
+TiledPlan tiled_band_plan(int Lx, int Ly, int sm_count);
 cudaError_t configure_tiled();
-int tiled_band_rows(int Ly, int sm_count);
-size_t tiled_smem_bytes(int Lx, int H);
-cudaError_t launch_tiled_phases(const SweepJob &job, int H, int k0, int n_sweeps, cudaStream_t stream);
+cudaError_t configure_band();
+cudaError_t launch_band_phases(const SweepJob &job, const TiledPlan &plan, const void *src, void *dst,
+                               int k, int f0, cudaStream_t stream);
+// Sweeps k0 .. k0 + n_sweeps - 1 of the plan.  With K >= 2 the launches alternate
+// between job.lat and alt (lat_bytes each) and end in job.lat (a copy back after
+// an odd number of launches).
+cudaError_t launch_tiled_phases(const SweepJob &job, const TiledPlan &plan, void *alt, size_t lat_bytes,
+                                int k0, int n_sweeps, cudaStream_t stream);
 cudaError_t launch_advance(long long *state, int n, cudaStream_t stream);
 cudaError_t launch_trace(long long *state, cudaStream_t stream);
 

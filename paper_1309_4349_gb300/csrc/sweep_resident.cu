@@ -492,6 +492,96 @@ resident_sweep_kernel(const SweepJob *__restrict__ jobs, const SweepCall *__rest
     }
 }
 
+// Tiled path, blocked: bands of H rows of a lattice too large for a cluster's
+// shared memory, one CTA each, K phases per launch.  A CTA loads its band and
+// D = 2K + 1 halo rows per side from the store `src` as it was at the launch's
+// start, advances K phases with the blocked phase code above (every flip local,
+// only the band's anchors counted), and writes its band to `dst`.  Reading one
+// buffer and writing the other keeps every CTA's halo at the launch's starting
+// state while other CTAs finish; the launch boundary orders the blocks.
+template <int THREADS>
+__global__ void __launch_bounds__(THREADS, 1)
+band_phases_kernel(const SweepJob J, const void *__restrict__ src, void *__restrict__ dst, int H, int K,
+                   int k, int f0)
+{
+    constexpr int kWarps = THREADS / 32;
+    extern __shared__ __align__(16) uint32_t lat[];
+    __shared__ PhaseR pp[8];
+    __shared__ uint64_t thr[16];
+    __shared__ long long red[5][kWarps];
+
+    Geo g;
+    g.Lx = J.Lx; g.Ly = J.Ly; g.W = J.W; g.RW = J.RW; g.magicW = J.magicW;
+    g.k0 = J.key0; g.k1 = J.key1;
+    g.zm1 = (J.geometry == kTRI6 ? 6 : 4) - 1;
+    g.sign = J.draw_lo > J.draw_hi ? 0 : (J.draw_lo == 0 ? -1 : 1);
+    g.C = (int)gridDim.x;
+    g.rank = (int)blockIdx.x;
+    g.Y0 = (int)blockIdx.x * H;
+    g.Y1 = min(g.Y0 + H, g.Ly);
+    g.prevY = g.prevH = g.nextY = g.nextH = 0;
+    g.lat_addr = smem_addr(lat);
+    g.D = 2 * K + 1;
+    g.base = g.Y0 - g.D < 0 ? g.Y0 - g.D + g.Ly : g.Y0 - g.D;
+    const int tid = threadIdx.x;
+    const int Hc = g.Y1 - g.Y0;
+    const int NL = Hc + 2 * g.D;
+    const long long s = J.state[kSweepBase] + k;
+    const uint32_t s_lo = (uint32_t)(unsigned long long)s;
+    const uint32_t s_hi = (uint32_t)((unsigned long long)s >> 32);
+
+    for (int idx = tid; idx < NL * g.RW; idx += THREADS) {
+        const int lr = idx / g.RW, w = idx - lr * g.RW;
+        int y = g.Y0 - g.D + lr;
+        if (y < 0) y += g.Ly;
+        if (y >= g.Ly) y -= g.Ly;
+        lat[idx] = padded_word(src, J.packing, J.pitch, y, w, g.Lx, g.W);
+    }
+    if (tid < 16) thr[tid] = J.thr[tid];
+    if (tid < K) phase_table(J, g, K, s, f0 + tid, &pp[tid]);
+    __syncthreads();
+
+    Acc A = {0u, 0u, 0u, 0u, 0};
+    for (int j = 0; j < K; ++j) {
+        const PhaseR P = pp[j];
+        if (J.geometry == kTRI6) run_phase_oi<kTRI6, THREADS, true>(lat, g, P, thr, f0 + j, s_lo, s_hi, A);
+        else run_phase_oi<kSQ4, THREADS, true>(lat, g, P, thr, f0 + j, s_lo, s_hi, A);
+        __syncthreads();
+    }
+
+    for (int idx = tid; idx < Hc * g.W; idx += THREADS) {
+        const int r = idx / g.W, w = idx - r * g.W;
+        const int y = g.Y0 + r;
+        const uint32_t v = lat[(size_t)(r + g.D) * g.RW + w + 1];
+        const int pos0 = 32 * w;
+        const int nvalid = min(32, g.Lx - pos0);
+        if (J.packing == kPackBit) {
+            const uint32_t valid = nvalid == 32 ? 0xFFFFFFFFu : ((1u << nvalid) - 1u);
+            ((uint32_t *)dst)[(size_t)y * J.pitch + w] = v & valid;
+        } else {
+            uint8_t *row = (uint8_t *)dst + (size_t)y * J.pitch;
+            for (int b = 0; b < nvalid; ++b) row[pos0 + b] = (uint8_t)((v >> b) & 1u);
+        }
+    }
+
+    long long vals[5] = {(long long)A.att, (long long)A.unl, (long long)A.drw, (long long)A.acc,
+                         (long long)A.dn};
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+        const long long ws = warp_sum(vals[q]);
+        if ((tid & 31) == 0) red[q][tid >> 5] = ws;
+    }
+    __syncthreads();
+    if (tid < 5) {
+        long long sum = 0;
+        for (int w = 0; w < kWarps; ++w) sum += red[tid][w];
+        if (sum != 0) {
+            const int slot = tid == 4 ? kNUnlike : kAttempts + tid;
+            atomicAdd((unsigned long long *)&J.state[slot], (unsigned long long)sum);
+        }
+    }
+}
+
 // Three variants: 512 threads (one CTA per SM; single lattices on one CTA), 256
 // threads with at most 128 registers (two CTAs per SM) and 128 threads with at
 // most 128 registers (four CTAs per SM; batches of many lattices).
@@ -591,6 +681,59 @@ cudaError_t launch_resident_sweep_one(const SweepJob &job, const SweepCall &call
                                       int threads, size_t smem_bytes, cudaStream_t stream)
 {
     return launch(nullptr, nullptr, nullptr, job, call, 1, cluster, threads, smem_bytes, stream);
+}
+
+#ifndef KLMC_TILED_BLOCK
+#define KLMC_TILED_BLOCK 4
+#endif
+#ifndef KLMC_BAND_THREADS
+#define KLMC_BAND_THREADS 1024
+#endif
+constexpr int kBandThreads = KLMC_BAND_THREADS;  // one CTA per SM
+
+TiledPlan tiled_band_plan(int Lx, int Ly, int sm_count)
+{
+    TiledPlan p;
+    const long long RW = (Lx + 95) / 32;
+    const long long max_rows = kResidentMaxSmem / (RW * 4);
+    for (int K = KLMC_TILED_BLOCK; K >= 2; K >>= 1) {
+        const int D = 2 * K + 1;
+        long long H = (Ly + sm_count - 1) / sm_count;  // one CTA per SM
+        if (H + 2 * D > max_rows) H = max_rows - 2 * D;  // more bands than SMs
+        if (H < 1 || H + 2 * D > Ly) continue;         // a band's rows must not wrap onto themselves
+        p.H = (int)H;
+        p.K = K;
+        p.threads = kBandThreads;
+        p.smem = (size_t)((H + 2 * D) * RW * 4);
+        return p;
+    }
+    p.H = 0;
+    p.K = 1;
+    p.threads = 0;
+    p.smem = 0;
+    return p;
+}
+
+cudaError_t configure_band()
+{
+    static thread_local int configured_device = -1;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (configured_device == dev) return cudaSuccess;
+    e = cudaFuncSetAttribute(band_phases_kernel<kBandThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             kResidentMaxSmem);
+    if (e == cudaSuccess) configured_device = dev;
+    return e;
+}
+
+cudaError_t launch_band_phases(const SweepJob &job, const TiledPlan &plan, const void *src, void *dst,
+                               int k, int f0, cudaStream_t stream)
+{
+    const int grid = (job.Ly + plan.H - 1) / plan.H;
+    band_phases_kernel<kBandThreads><<<grid, kBandThreads, plan.smem, stream>>>(job, src, dst, plan.H, plan.K, k,
+                                                                               f0);
+    return cudaGetLastError();
 }
 
 }  // namespace klmc

@@ -184,29 +184,49 @@ __global__ void trace_kernel(long long *state)
 
 cudaError_t configure_tiled()
 {
-    return cudaFuncSetAttribute(tiled_phase_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)(227 * 1024 - 2048));
+    cudaError_t e = cudaFuncSetAttribute(tiled_phase_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(227 * 1024 - 2048));
+    if (e == cudaSuccess) e = configure_band();
+    return e;
 }
 
-int tiled_band_rows(int Ly, int sm_count)
+TiledPlan tiled_plan(int Lx, int Ly, int sm_count)
 {
+    TiledPlan p = tiled_band_plan(Lx, Ly, sm_count);
+    if (p.K >= 2) return p;
     int h = (Ly + 2 * sm_count - 1) / (2 * sm_count);
-    return h < 4 ? 4 : h;
+    p.H = h < 4 ? 4 : h;
+    p.K = 1;
+    p.threads = kThreads;
+    p.smem = (size_t)((Lx + 95) / 32) * (size_t)(p.H + 4) * sizeof(uint32_t);
+    return p;
 }
 
-size_t tiled_smem_bytes(int Lx, int H)
+cudaError_t launch_tiled_phases(const SweepJob &job, const TiledPlan &plan, void *alt, size_t lat_bytes,
+                                int k0, int n_sweeps, cudaStream_t stream)
 {
-    return (size_t)((Lx + 95) / 32) * (size_t)(H + 4) * sizeof(uint32_t);
-}
-
-cudaError_t launch_tiled_phases(const SweepJob &job, int H, int k0, int n_sweeps, cudaStream_t stream)
-{
-    const int grid = (job.Ly + H - 1) / H;
-    const size_t smem = tiled_smem_bytes(job.Lx, H);
-    for (int k = 0; k < n_sweeps; ++k)
-        for (int f = 0; f < 8; ++f)
-            tiled_phase_kernel<<<grid, kThreads, smem, stream>>>(job, H, k0 + k, f);
-    return cudaGetLastError();
+    const int grid = (job.Ly + plan.H - 1) / plan.H;
+    if (plan.K < 2) {
+        for (int k = 0; k < n_sweeps; ++k)
+            for (int f = 0; f < 8; ++f)
+                tiled_phase_kernel<<<grid, kThreads, plan.smem, stream>>>(job, plan.H, k0 + k, f);
+        return cudaGetLastError();
+    }
+    const void *src = job.lat;
+    void *dst = alt;
+    int launches = 0;
+    for (int k = 0; k < n_sweeps; ++k) {
+        for (int f0 = 0; f0 < 8; f0 += plan.K) {
+            cudaError_t e = launch_band_phases(job, plan, src, dst, k0 + k, f0, stream);
+            if (e != cudaSuccess) return e;
+            void *t = (void *)src;
+            src = dst;
+            dst = t;
+            ++launches;
+        }
+    }
+    if (launches & 1) return cudaMemcpyAsync(job.lat, alt, lat_bytes, cudaMemcpyDeviceToDevice, stream);
+    return cudaSuccess;
 }
 
 cudaError_t launch_advance(long long *state, int n, cudaStream_t stream)

@@ -110,6 +110,21 @@ def test_tiled_path_parity(geometry, packing, Lx, Ly, nA, bw, n_mcs, trace_every
     assert_same_run(lat, ref)
 
 
+@pytest.mark.parametrize("packing", PACKS)
+@pytest.mark.parametrize("Lx,Ly,K", [(200, 777, 4), (60000, 64, 4), (200000, 16, 1), (5, 7, 1), (64, 64, 4)])
+def test_tiled_plans(packing, Lx, Ly, K):
+    """The tiled path's plans: blocks of K phases per launch over bands of one or
+    more rows, with rows wider than 2000 words, and the per-phase kernel when no
+    block of halo rows fits (too short, or rows too wide for 2 x 5 halo rows in
+    shared memory).  Odd sweep counts end the ping-pong on the second buffer."""
+    nA, bw, seed = Lx * Ly * 2 // 5, 0.9, 31 + Ly
+    lat = make(Lx, Ly, nA, bw, seed, klmc.TRI6, packing, cluster=-1)
+    assert lat.plan() == K
+    lat.sweep(3)
+    ref = oracle.run(Lx, Ly, klmc.TRI6, bw, seed, oracle.init(Lx, Ly, nA, seed), 0, 3)
+    assert_same_run(lat, ref)
+
+
 def test_tiled_split_equals_whole():
     Lx, Ly, nA, bw, seed = 90, 70, 2000, 0.7, 44
     a = make(Lx, Ly, nA, bw, seed, cluster=-1)
