@@ -36,30 +36,65 @@ __device__ __forceinline__ Philox4 philox4(uint32_t c0, uint32_t c1, uint32_t c2
     return out;
 }
 
-// Word 0 of Philox4x32-10 for two counters that differ only in word 0, computed
-// in lockstep so the two dependency chains overlap.
-__device__ __forceinline__ void philox2_w0(uint32_t a0, uint32_t b0, uint32_t c1, uint32_t c2,
-                                           uint32_t c3, uint32_t k0, uint32_t k1, uint32_t &ra,
-                                           uint32_t &rb)
+// The draws of one phase use counters {site, f, s_lo, s_hi} that differ only in
+// word 0.  In the first two rounds the products that do not depend on word 0 --
+// s_lo * M1 in round 0 and, from it, the round-1 product of the new word 0 -- are
+// the same for every draw of the phase; DrawKey holds them (with the round keys
+// folded in) so that a draw pays two fewer multiplications.
+struct DrawKey {
+    uint32_t sk;  // s_hi ^ k1                       (round 0, word 2)
+    uint32_t bk;  // lo(s_lo * M1) ^ (k0 + W0)       (round 1, word 0)
+    uint32_t hk;  // hi(A * M0) ^ (k1 + W1), A = hi(s_lo * M1) ^ f ^ k0   (round 1, word 2)
+    uint32_t la;  // lo(A * M0)                      (round 1, word 3)
+    uint32_t k0, k1;
+};
+
+__device__ __forceinline__ DrawKey draw_key(uint32_t f, uint32_t s_lo, uint32_t s_hi, uint32_t k0, uint32_t k1)
 {
-    uint32_t a1 = c1, a2 = c2, a3 = c3, b1 = c1, b2 = c2, b3 = c3;
+    const unsigned long long p1 = (unsigned long long)s_lo * 0xCD9E8D57ull;
+    const uint32_t A = (uint32_t)(p1 >> 32) ^ f ^ k0;
+    const unsigned long long pa = (unsigned long long)A * 0xD2511F53ull;
+    DrawKey d;
+    d.sk = s_hi ^ k1;
+    d.bk = (uint32_t)p1 ^ (k0 + 0x9E3779B9u);
+    d.hk = (uint32_t)(pa >> 32) ^ (k1 + 0xBB67AE85u);
+    d.la = (uint32_t)pa;
+    d.k0 = k0;
+    d.k1 = k1;
+    return d;
+}
+
+// Word 0 of Philox4x32-10 at counters {a0, f, s_lo, s_hi} and {b0, f, s_lo, s_hi}
+// (the phase's DrawKey), the two chains in lockstep.
+__device__ __forceinline__ void philox2_w0_key(uint32_t a0, uint32_t b0, const DrawKey &d, uint32_t &ra,
+                                               uint32_t &rb)
+{
+    // rounds 0 and 1 with the phase constants
+    const unsigned long long qa = (unsigned long long)a0 * 0xD2511F53ull;
+    const unsigned long long qb = (unsigned long long)b0 * 0xD2511F53ull;
+    const uint32_t a2r = (uint32_t)(qa >> 32) ^ d.sk, b2r = (uint32_t)(qb >> 32) ^ d.sk;
+    const unsigned long long ta = (unsigned long long)a2r * 0xCD9E8D57ull;
+    const unsigned long long tb = (unsigned long long)b2r * 0xCD9E8D57ull;
+    uint32_t xa0 = (uint32_t)(ta >> 32) ^ d.bk, xa1 = (uint32_t)ta, xa2 = d.hk ^ (uint32_t)qa, xa3 = d.la;
+    uint32_t xb0 = (uint32_t)(tb >> 32) ^ d.bk, xb1 = (uint32_t)tb, xb2 = d.hk ^ (uint32_t)qb, xb3 = d.la;
+    uint32_t k0 = d.k0 + 2u * 0x9E3779B9u, k1 = d.k1 + 2u * 0xBB67AE85u;
 #pragma unroll
-    for (int r = 0; r < 10; ++r) {
-        const unsigned long long pa0 = (unsigned long long)a0 * 0xD2511F53ull;
-        const unsigned long long pa1 = (unsigned long long)a2 * 0xCD9E8D57ull;
-        const unsigned long long pb0 = (unsigned long long)b0 * 0xD2511F53ull;
-        const unsigned long long pb1 = (unsigned long long)b2 * 0xCD9E8D57ull;
-        const uint32_t na0 = (uint32_t)(pa1 >> 32) ^ a1 ^ k0;
-        const uint32_t na2 = (uint32_t)(pa0 >> 32) ^ a3 ^ k1;
-        const uint32_t nb0 = (uint32_t)(pb1 >> 32) ^ b1 ^ k0;
-        const uint32_t nb2 = (uint32_t)(pb0 >> 32) ^ b3 ^ k1;
-        a1 = (uint32_t)pa1; a3 = (uint32_t)pa0; a0 = na0; a2 = na2;
-        b1 = (uint32_t)pb1; b3 = (uint32_t)pb0; b0 = nb0; b2 = nb2;
+    for (int r = 2; r < 10; ++r) {
+        const unsigned long long pa0 = (unsigned long long)xa0 * 0xD2511F53ull;
+        const unsigned long long pa1 = (unsigned long long)xa2 * 0xCD9E8D57ull;
+        const unsigned long long pb0 = (unsigned long long)xb0 * 0xD2511F53ull;
+        const unsigned long long pb1 = (unsigned long long)xb2 * 0xCD9E8D57ull;
+        const uint32_t na0 = (uint32_t)(pa1 >> 32) ^ xa1 ^ k0;
+        const uint32_t na2 = (uint32_t)(pa0 >> 32) ^ xa3 ^ k1;
+        const uint32_t nb0 = (uint32_t)(pb1 >> 32) ^ xb1 ^ k0;
+        const uint32_t nb2 = (uint32_t)(pb0 >> 32) ^ xb3 ^ k1;
+        xa1 = (uint32_t)pa1; xa3 = (uint32_t)pa0; xa0 = na0; xa2 = na2;
+        xb1 = (uint32_t)pb1; xb3 = (uint32_t)pb0; xb0 = nb0; xb2 = nb2;
         k0 += 0x9E3779B9u;
         k1 += 0xBB67AE85u;
     }
-    ra = a0;
-    rb = b0;
+    ra = xa0;
+    rb = xb0;
 }
 
 __device__ __forceinline__ int floor_div(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
@@ -323,8 +358,7 @@ __device__ __forceinline__ void evaluate(const uint32_t *r0, int RW, int j, uint
 // Accept bits of the positions in dmask, each drawing Philox word 0 of counter
 // {site_base + p, f, s_lo, s_hi}; two evaluations interleaved at a time.
 __device__ __forceinline__ uint32_t draw_accepts(uint32_t dmask, const Planes &S,
-                                                 uint32_t site_base, uint32_t f, uint32_t s_lo,
-                                                 uint32_t s_hi, uint32_t k0, uint32_t k1,
+                                                 uint32_t site_base, const DrawKey &dk,
                                                  const uint64_t *thr)
 {
     uint32_t acc = 0u;
@@ -335,7 +369,7 @@ __device__ __forceinline__ uint32_t draw_accepts(uint32_t dmask, const Planes &S
         const int p2 = dm != 0u ? __ffs(dm) - 1 : p1;  // an odd last draw is repeated
         dm &= dm - 1u;
         uint32_t r1, r2;
-        philox2_w0(site_base + (uint32_t)p1, site_base + (uint32_t)p2, f, s_lo, s_hi, k0, k1, r1, r2);
+        philox2_w0_key(site_base + (uint32_t)p1, site_base + (uint32_t)p2, dk, r1, r2);
         const uint32_t S1 = ((S.s0 >> p1) & 1u) | (((S.s1 >> p1) & 1u) << 1) |
                             (((S.s2 >> p1) & 1u) << 2) | (((S.s3 >> p1) & 1u) << 3);
         const uint32_t S2 = ((S.s0 >> p2) & 1u) | (((S.s1 >> p2) & 1u) << 1) |

@@ -175,6 +175,7 @@ __device__ __forceinline__ void run_phase(const uint32_t *lat, const Geo &g, con
     // (At 512 threads the extra evaluations cost more issue slots than they save.)
     const int ls = THREADS > 256 ? 0 : (4 * P.ntask <= THREADS ? 2 : (2 * P.ntask <= THREADS ? 1 : 0));
     const int nlane = P.ntask << ls;
+    const DrawKey dk = draw_key((uint32_t)f, s_lo, s_hi, g.k0, g.k1);
     for (int t0 = threadIdx.x & ~31; t0 < nlane; t0 += THREADS) {
         const int tl = t0 + lane;
         uint32_t am = 0u, ta = 0u, tb = 0u;
@@ -206,8 +207,7 @@ __device__ __forceinline__ void run_phase(const uint32_t *lat, const Geo &g, con
         const uint32_t dmask = unl & draw_positions<G>(S, g.sign);
         uint32_t acc = unl & ~dmask;
 
-        acc |= draw_accepts(dmask, S, (uint32_t)(y * g.Lx + x0), (uint32_t)f, s_lo, s_hi, g.k0,
-                            g.k1, thr);
+        acc |= draw_accepts(dmask, S, (uint32_t)(y * g.Lx + x0), dk, thr);
         const bool own = !BLOCKED || (unsigned)(lr - g.D) < (unsigned)H;
         if (own) {
             A.att += __popc(am);

@@ -56,6 +56,7 @@ __device__ __forceinline__ void run_tiles(const uint32_t *tile, const SweepJob &
 {
     constexpr int bdy = OI == 0 ? 0 : (OI == 1 ? 1 : -1);
     constexpr int bdx = OI == 1 ? 0 : 1;
+    const DrawKey dk = draw_key((uint32_t)f, s_lo, s_hi, J.key0, J.key1);
     for (int t = threadIdx.x; t < P.ntask; t += kThreads) {
         const int mi = (int)(((unsigned long long)t * J.magicW) >> 32);
         const int j = t - mi * J.W;
@@ -71,8 +72,7 @@ __device__ __forceinline__ void run_tiles(const uint32_t *tile, const SweepJob &
         const uint32_t unl = (ta ^ tb) & am;
         const uint32_t dmask = unl & draw_positions<G>(S, sign);
         uint32_t acc = unl & ~dmask;
-        acc |= draw_accepts(dmask, S, (uint32_t)(y * J.Lx + x0), (uint32_t)f, s_lo, s_hi, J.key0,
-                            J.key1, thr);
+        acc |= draw_accepts(dmask, S, (uint32_t)(y * J.Lx + x0), dk, thr);
         A.att += __popc(am);
         A.unl += __popc(unl);
         A.drw += __popc(dmask);
