@@ -59,11 +59,15 @@ C_PHILOX = 40.0
 # paper_1309_4349_gb300/probes/int_peak.cu measures 60 LOP3 and 30 IMAD.WIDE
 # (+30 LOP3) lane-ops/clk/SM on GB300, i.e. one 64-lane integer pipe.
 INT32_LANES_PER_SM = 64
-# DRAM bytes (read + write) of one resident-sweep launch of this workload from one ncu
-# capture (profiles/resident_sweep_400x400x5_ncu.md), valid only for the kernel
-# sources it was taken with (hash of sweep_resident.cu + sweep_common.cuh).
-TRAFFIC_C2_LAUNCH = 209408
-TRAFFIC_C2_SOURCES = "da1cb40eefd0810d"
+# DRAM bytes (read + write) per launch of the dominant kernel, from one ncu capture
+# each (profiles/resident_sweep_400x400x5_ncu.md: one resident-sweep launch of 500 MCS
+# of the 400x400 x 5 workload; profiles/band_phases_8192x8192_ncu.md: one 4-phase band
+# launch of the 8192x8192 lattice), valid only for the kernel sources they were taken
+# with (hash of sweep_resident.cu + sweep_common.cuh).
+TRAFFIC_C2_LAUNCH = 209920
+TRAFFIC_C3_LAUNCH = 8459264
+TRAFFIC_SOURCES = "a1e32b4a26bcfeb0"
+
 
 
 def resident_sources_hash() -> str:
@@ -423,7 +427,11 @@ def bench_other(args, klmc, torch, np):
                            attempts // launches, cnt["draws"] / attempts, sm_count,
                            clk["sm_mhz"] if clk else 2070.0, -1,
                            {"note": "per-launch time = step time / sweep launches (graph replays)",
-                            "phases_per_launch": K})
+                            "phases_per_launch": K,
+                            "traffic": (TRAFFIC_C3_LAUNCH if resident_sources_hash() == TRAFFIC_SOURCES
+                                        and geom == klmc.TRI6 else None),
+                            "traffic_note": "DRAM bytes per launch from one ncu capture (TRI6); the "
+                                            "8 MiB lattice and its second buffer stay in L2"})
             v = {"value": attempts / (ms_step * 1e-3), "ms_per_step": ms_step, "roofline": rl,
                  "clocks": clk, "final_n_unlike": int(trace[-1].item())}
             line["variants"][name] = v
@@ -625,7 +633,7 @@ def main():
     ctas = nrun * cluster
     roofline = {"bound": "alu", "kernel": "resident_sweep_kernel", "achieved": achieved_tops,
                 "peak": peak_tops, "unit": "Tops/s (INT32 lane-ops)", "frac": achieved_tops / peak_tops,
-                "traffic": (TRAFFIC_C2_LAUNCH if resident_sources_hash() == TRAFFIC_C2_SOURCES
+                "traffic": (TRAFFIC_C2_LAUNCH if resident_sources_hash() == TRAFFIC_SOURCES
                             and n_mcs % HIST_EVERY == 0 else None),
                 "traffic_note": "DRAM bytes per launch from one ncu capture (cold cache); the "
                                 "lattices stay in shared memory within a launch",
