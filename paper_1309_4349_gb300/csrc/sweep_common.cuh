@@ -380,6 +380,57 @@ __device__ __forceinline__ uint32_t draw_accepts(uint32_t dmask, const Planes &S
     return acc;
 }
 
+// Accept bits of this lane's dmask when the warp's draws are drawn by all its
+// lanes.  Every lane appends its draws (site index, S, bit, lane) to the warp's
+// queue q at its prefix-sum offset; then lane i draws entries i and i + 32 of
+// every 64 (two Philox chains interleaved) and returns accepted bits to their
+// lanes through wacc (the warp's 32 words of shared memory, zero on entry and on
+// return).  When the warp has more than kDrawQueue draws, each lane draws its own.
+// Every lane of the warp must call it.
+constexpr int kDrawQueue = 256;
+
+__device__ __forceinline__ uint32_t draw_accepts_queue(uint32_t dmask, const Planes &S, uint32_t site_base,
+                                                       const DrawKey &dk, const uint64_t *thr, uint2 *q,
+                                                       uint32_t *wacc)
+{
+    if (!__any_sync(0xFFFFFFFFu, dmask != 0u)) return 0u;
+    const int lane = (int)(threadIdx.x & 31);
+    const int nd = __popc(dmask);
+    int incl = nd;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    const int total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+    if (total > kDrawQueue) return draw_accepts(dmask, S, site_base, dk, thr);
+    int slot = incl - nd;
+    uint32_t dm = dmask;
+    while (dm != 0u) {
+        const int p = __ffs(dm) - 1;
+        dm &= dm - 1u;
+        const uint32_t Sp = ((S.s0 >> p) & 1u) | (((S.s1 >> p) & 1u) << 1) | (((S.s2 >> p) & 1u) << 2) |
+                            (((S.s3 >> p) & 1u) << 3);
+        q[slot++] = make_uint2(site_base + (uint32_t)p, Sp | ((uint32_t)p << 4) | ((uint32_t)lane << 9));
+    }
+    __syncwarp();
+    for (int k = lane; k < total; k += 64) {
+        const uint2 e1 = q[k];
+        const bool two = k + 32 < total;
+        const uint2 e2 = two ? q[k + 32] : e1;
+        uint32_t r1, r2;
+        philox2_w0_key(e1.x, e2.x, dk, r1, r2);
+        if ((uint64_t)r1 < thr[e1.y & 15u]) atomicOr(wacc + ((e1.y >> 9) & 31u), 1u << ((e1.y >> 4) & 31u));
+        if (two && (uint64_t)r2 < thr[e2.y & 15u])
+            atomicOr(wacc + ((e2.y >> 9) & 31u), 1u << ((e2.y >> 4) & 31u));
+    }
+    __syncwarp();
+    const uint32_t acc = wacc[lane];
+    wacc[lane] = 0u;
+    __syncwarp();
+    return acc;
+}
+
 // One padded shared-memory row from the device store (see the row layout above):
 // word 0 holds position -1 (site Lx-1) in bit 31; words 1..W hold sites 0..Lx-1;
 // positions Lx, Lx+1 hold sites 0, 1; every other pad bit is zero.

@@ -162,7 +162,8 @@ __device__ __forceinline__ void phase_barrier(int C)
 template <int G, int OI, int THREADS, bool BLOCKED>
 __device__ __forceinline__ void run_phase(const uint32_t *lat, const Geo &g, const PhaseR &P,
                                           const uint64_t *thr, int f,
-                                          uint32_t s_lo, uint32_t s_hi, Acc &A)
+                                          uint32_t s_lo, uint32_t s_hi, Acc &A, uint2 *dq = nullptr,
+                                          uint32_t *wacc = nullptr)
 {
     // b = a + o: (1,0) -> same row, +1; (0,1) -> next row; (1,-1) -> previous row, +1
     constexpr int bdy = OI == 0 ? 0 : (OI == 1 ? 1 : -1);
@@ -207,7 +208,10 @@ __device__ __forceinline__ void run_phase(const uint32_t *lat, const Geo &g, con
         const uint32_t dmask = unl & draw_positions<G>(S, g.sign);
         uint32_t acc = unl & ~dmask;
 
-        acc |= draw_accepts(dmask, S, (uint32_t)(y * g.Lx + x0), dk, thr);
+        if (dq != nullptr)
+            acc |= draw_accepts_queue(dmask, S, (uint32_t)(y * g.Lx + x0), dk, thr, dq, wacc);
+        else
+            acc |= draw_accepts(dmask, S, (uint32_t)(y * g.Lx + x0), dk, thr);
         const bool own = !BLOCKED || (unsigned)(lr - g.D) < (unsigned)H;
         if (own) {
             A.att += __popc(am);
@@ -261,11 +265,12 @@ __device__ __forceinline__ void run_phase(const uint32_t *lat, const Geo &g, con
 template <int G, int THREADS, bool BLOCKED>
 __device__ __forceinline__ void run_phase_oi(const uint32_t *lat, const Geo &g, const PhaseR &P,
                                              const uint64_t *thr, int f, uint32_t s_lo,
-                                             uint32_t s_hi, Acc &A)
+                                             uint32_t s_hi, Acc &A, uint2 *dq = nullptr,
+                                             uint32_t *wacc = nullptr)
 {
-    if (P.oi == 0) run_phase<G, 0, THREADS, BLOCKED>(lat, g, P, thr, f, s_lo, s_hi, A);
-    else if (G == kTRI6 && P.oi == 2) run_phase<G, 2, THREADS, BLOCKED>(lat, g, P, thr, f, s_lo, s_hi, A);
-    else run_phase<G, 1, THREADS, BLOCKED>(lat, g, P, thr, f, s_lo, s_hi, A);
+    if (P.oi == 0) run_phase<G, 0, THREADS, BLOCKED>(lat, g, P, thr, f, s_lo, s_hi, A, dq, wacc);
+    else if (G == kTRI6 && P.oi == 2) run_phase<G, 2, THREADS, BLOCKED>(lat, g, P, thr, f, s_lo, s_hi, A, dq, wacc);
+    else run_phase<G, 1, THREADS, BLOCKED>(lat, g, P, thr, f, s_lo, s_hi, A, dq, wacc);
 }
 
 template <typename T>
@@ -290,8 +295,8 @@ __device__ __forceinline__ uint32_t cluster_ctarank()
     return v;
 }
 
-// Dynamic shared memory a CTA may use (the kernel's static arrays take under 2 KB).
-constexpr int kResidentMaxSmem = 227 * 1024 - 3072;
+// Dynamic shared memory a CTA may use (the kernels' static arrays take under 6 KB).
+constexpr int kResidentMaxSmem = 227 * 1024 - 6144;
 
 #ifndef KLMC_MAX_BLOCK
 #define KLMC_MAX_BLOCK 4
@@ -509,6 +514,8 @@ band_phases_kernel(const SweepJob J, const void *__restrict__ src, void *__restr
     __shared__ PhaseR pp[8];
     __shared__ uint64_t thr[16];
     __shared__ long long red[5][kWarps];
+    __shared__ uint32_t wacc_all[THREADS];  // per-warp accept words of queued draws
+    wacc_all[threadIdx.x] = 0u;
 
     Geo g;
     g.Lx = J.Lx; g.Ly = J.Ly; g.W = J.W; g.RW = J.RW; g.magicW = J.magicW;
@@ -542,10 +549,14 @@ band_phases_kernel(const SweepJob J, const void *__restrict__ src, void *__restr
     __syncthreads();
 
     Acc A = {0u, 0u, 0u, 0u, 0};
+    // the warps' draw queues follow the rows (H + 2D rows of the tallest band)
+    uint2 *const dq = (uint2 *)(lat + (((size_t)(H + 2 * g.D) * g.RW + 1) & ~(size_t)1)) +
+                      (size_t)(tid >> 5) * kDrawQueue;
+    uint32_t *const wacc = wacc_all + (tid & ~31);
     for (int j = 0; j < K; ++j) {
         const PhaseR P = pp[j];
-        if (J.geometry == kTRI6) run_phase_oi<kTRI6, THREADS, true>(lat, g, P, thr, f0 + j, s_lo, s_hi, A);
-        else run_phase_oi<kSQ4, THREADS, true>(lat, g, P, thr, f0 + j, s_lo, s_hi, A);
+        if (J.geometry == kTRI6) run_phase_oi<kTRI6, THREADS, true>(lat, g, P, thr, f0 + j, s_lo, s_hi, A, dq, wacc);
+        else run_phase_oi<kSQ4, THREADS, true>(lat, g, P, thr, f0 + j, s_lo, s_hi, A, dq, wacc);
         __syncthreads();
     }
 
@@ -695,7 +706,8 @@ TiledPlan tiled_band_plan(int Lx, int Ly, int sm_count)
 {
     TiledPlan p;
     const long long RW = (Lx + 95) / 32;
-    const long long max_rows = kResidentMaxSmem / (RW * 4);
+    const long long queue_bytes = (long long)kBandThreads / 32 * kDrawQueue * 8 + 8;
+    const long long max_rows = (kResidentMaxSmem - queue_bytes) / (RW * 4);
     for (int K = KLMC_TILED_BLOCK; K >= 2; K >>= 1) {
         const int D = 2 * K + 1;
         long long H = (Ly + sm_count - 1) / sm_count;  // one CTA per SM
@@ -704,7 +716,7 @@ TiledPlan tiled_band_plan(int Lx, int Ly, int sm_count)
         p.H = (int)H;
         p.K = K;
         p.threads = kBandThreads;
-        p.smem = (size_t)((H + 2 * D) * RW * 4);
+        p.smem = (size_t)((((H + 2 * D) * RW + 1) & ~1ll) * 4 + (long long)kBandThreads / 32 * kDrawQueue * 8);
         return p;
     }
     p.H = 0;
