@@ -110,6 +110,22 @@ def dist_info():
     return rank, world, local
 
 
+def replica_seeds(rank):
+    """Seeds of one rank's copy of the workload: every rank runs independent
+    Markov chains (replicas only; no collective on the data path)."""
+    return [s + 1000 * rank for s in SEEDS]
+
+
+def max_over_ranks(x, dist, device):
+    """The largest x over all ranks (x itself without a process group)."""
+    import torch
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 class ClockSampler:
     """nvidia-smi clock/throttle samples during the timed region."""
 
@@ -200,7 +216,8 @@ def oracle_sample(n_mcs: int, threads: int):
     return sum(res), dt
 
 
-def run_reference(args, rank):
+def run_reference(args, rank, world=1):
+    """The oracle timed on the host's cores; under torchrun rank 0 alone runs it."""
     if rank != 0:
         return
     n_mcs = 60
@@ -216,10 +233,11 @@ def run_reference(args, rank):
               f"one host thread per run")
     line = {
         "impl": "reference", "metric": "Kawasaki exchange attempts/s", "value": value,
-        "unit": "attempts/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "unit": "attempts/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "form": "oracle (plain sequential C, CPU)"},
+        "config": {"workload": WORKLOAD, "form": "oracle (plain sequential C, CPU)",
+                   "ranks": "rank 0 only" if world > 1 else "single process"},
         "cpu_baseline": {"value": value, "unit": "attempts/s", "cores": len(SEEDS),
                          "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "attempts/s", "h2d_bytes_per_step": 0,
@@ -496,7 +514,7 @@ def main():
     args = parse()
     rank, world, local = dist_info()
     if args.impl == "reference":
-        run_reference(args, rank)
+        run_reference(args, rank, world)
         return
 
     import numpy as np
@@ -529,7 +547,7 @@ def main():
     n_mcs = args.mcs
     n_seg = n_mcs // HIST_EVERY
     assert n_seg * HIST_EVERY == n_mcs
-    seeds = [s + 1000 * rank for s in SEEDS]
+    seeds = replica_seeds(rank)
     reps = [dict(Lx=L, Ly=L, fraction_A=FRACTION_A, omega_over_kT=w, seed=s,
                  packing=klmc.PACK_BIT) for w, s in zip(OMEGAS, seeds)]
     nrun = len(reps)
@@ -613,11 +631,7 @@ def main():
     attempts_step = sum(c["attempts"] for c in cnt)
     draws_step = sum(c["draws"] for c in cnt)
     assert attempts_step == nrun * n_mcs * N, attempts_step  # 4 | 400: N attempts per MCS
-    # max over ranks of the device time
-    t = torch.tensor([ms_step], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_step_max = float(t.item())
+    ms_step_max = max_over_ranks(ms_step, dist, "cuda")  # device time, max over ranks
     value = world * attempts_step / (ms_step_max * 1e-3)
 
     sweep_ms = [e0.elapsed_time(e1) for e0, e1 in sweep_events]
@@ -685,11 +699,7 @@ def main():
     for _ in range(args.steps):
         step_e2e()
     torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - t0) / args.steps
-    t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    e2e_s = float(t.item())
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / args.steps, dist, "cuda")
     h2d = nrun * N
     d2h = sizes.numel() * 8 + counts.numel() * 8 + ndist.numel() * 8 + nrun * N + nrun * 8
     e2e = {"value": world * attempts_step / e2e_s, "unit": "attempts/s", "h2d_bytes_per_step": h2d,
