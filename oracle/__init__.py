@@ -28,6 +28,7 @@ _lock = threading.Lock()
 _lib = None
 
 TRI6, SQ4 = 0, 1
+PERIODIC, HELICAL = 0, 1
 COORDINATION = {TRI6: 6, SQ4: 4}
 # Bond orientations, every bond is {i, i+o} for one site i (section "Monte Carlo
 # model with Kawasaki based kinetics", Fig. 2: triangular lattice; square option).
@@ -84,6 +85,19 @@ def _load():
     lib.orc_run_random_sequential.argtypes = [i32, i32, i32, dbl, u64, vp, i64, i64,
                                               ctypes.POINTER(i64), ctypes.POINTER(i64)]
     lib.orc_run_random_sequential.restype = ctypes.c_int
+    lib.orc_n_unlike_b.argtypes = [i32, i32, i32, i32, vp]
+    lib.orc_n_unlike_b.restype = i64
+    lib.orc_helical_valid.argtypes = [i32, i32]
+    lib.orc_helical_valid.restype = ctypes.c_int
+    lib.orc_mpkk_params.argtypes = [u64, i64, i32, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+    lib.orc_mpkk_params.restype = None
+    lib.orc_run_mpkk.argtypes = [i32, i32, dbl, u64, vp, i64, i64, ctypes.POINTER(i64), vp, i64, vp,
+                                 ctypes.c_int]
+    lib.orc_run_mpkk.restype = ctypes.c_int
+    lib.orc_cluster_labels_b.argtypes = [i32, i32, i32, i32, vp, ctypes.c_int, vp]
+    lib.orc_cluster_labels_b.restype = i64
+    lib.orc_cluster_histogram_b.argtypes = [i32, i32, i32, i32, vp, ctypes.c_int, vp, vp, i64]
+    lib.orc_cluster_histogram_b.restype = i64
     _lib = lib
     return lib
 
@@ -137,10 +151,10 @@ def init(Lx: int, Ly: int, nA: int, seed: int) -> np.ndarray:
     return t
 
 
-def n_unlike(Lx: int, Ly: int, geometry: int, t: np.ndarray) -> int:
+def n_unlike(Lx: int, Ly: int, geometry: int, t: np.ndarray, boundary: int = PERIODIC) -> int:
     """Number of unlike nearest-neighbour contacts; E/kT = (omega/kT) * n_unlike."""
     t = np.ascontiguousarray(t, dtype=np.uint8)
-    return int(_load().orc_n_unlike(Lx, Ly, geometry, _ptr(t)))
+    return int(_load().orc_n_unlike_b(Lx, Ly, geometry, boundary, _ptr(t)))
 
 
 def phase_params(Lx: int, Ly: int, geometry: int, seed: int, sweep: int, phase: int):
@@ -195,26 +209,68 @@ def run(Lx: int, Ly: int, geometry: int, bw: float, seed: int, lattice: np.ndarr
     return RunResult(t, nu.value, cnt, trace[:n_tr])
 
 
-def cluster_labels(Lx: int, Ly: int, geometry: int, t: np.ndarray, species: int = 1):
+def cluster_labels(Lx: int, Ly: int, geometry: int, t: np.ndarray, species: int = 1,
+                   boundary: int = PERIODIC):
     """Component label (smallest site index of the component) per site of the
     species, -1 elsewhere (section "Cluster Analysis methods")."""
     t = np.ascontiguousarray(t, dtype=np.uint8)
     labels = np.zeros(Lx * Ly, dtype=np.int64)
-    n = _load().orc_cluster_labels(Lx, Ly, geometry, _ptr(t), species, _ptr(labels))
+    n = _load().orc_cluster_labels_b(Lx, Ly, geometry, boundary, _ptr(t), species, _ptr(labels))
     return labels, int(n)
 
 
-def cluster_histogram(Lx: int, Ly: int, geometry: int, t: np.ndarray, species: int = 1):
+def cluster_histogram(Lx: int, Ly: int, geometry: int, t: np.ndarray, species: int = 1,
+                      boundary: int = PERIODIC):
     """Sparse ascending (sizes, counts) of the species' clusters."""
     lib = _load()
     t = np.ascontiguousarray(t, dtype=np.uint8)
-    n = lib.orc_cluster_histogram(Lx, Ly, geometry, _ptr(t), species, None, None, 0)
+    n = lib.orc_cluster_histogram_b(Lx, Ly, geometry, boundary, _ptr(t), species, None, None, 0)
     if n < 0:
         raise MemoryError("orc_cluster_histogram")
     sizes = np.zeros(max(n, 1), dtype=np.int64)
     counts = np.zeros(max(n, 1), dtype=np.int64)
-    lib.orc_cluster_histogram(Lx, Ly, geometry, _ptr(t), species, _ptr(sizes), _ptr(counts), n)
+    lib.orc_cluster_histogram_b(Lx, Ly, geometry, boundary, _ptr(t), species, _ptr(sizes), _ptr(counts), n)
     return sizes[:n], counts[:n]
+
+
+# ---------------------------------------------------------------------------
+# Helical boundary and the seven-colour schedule (section "Massive Parallel
+# Kawasaki Kinetics": seven-lipid domains, helical boundary conditions, the MPKK
+# loop with k = rand%7 per iteration).
+# ---------------------------------------------------------------------------
+def helical_valid(Lx: int, Ly: int) -> bool:
+    """Whether the seven domain coverages tile the helical Lx x Ly lattice."""
+    return bool(_load().orc_helical_valid(Lx, Ly))
+
+
+def mpkk_params(seed: int, sweep: int, phase: int):
+    """(coverage k, direction index d) of iteration `phase` of sweep `sweep`."""
+    k, d = ctypes.c_int(), ctypes.c_int()
+    _load().orc_mpkk_params(seed, sweep, phase, ctypes.byref(k), ctypes.byref(d))
+    return k.value, d.value
+
+
+def run_mpkk(Lx: int, Ly: int, bw: float, seed: int, lattice: np.ndarray, sweep0: int, n_mcs: int,
+             n_unlike0: int | None = None, counters0=(0, 0, 0, 0), trace_every: int = 0,
+             check: bool = False, reverse: bool = False) -> RunResult:
+    """n_mcs sweeps of seven iterations each on the helical triangular lattice:
+    per iteration a random coverage by seven-lipid domains and one Kawasaki
+    attempt per domain (MPKK loop), all domains in one shared direction."""
+    lib = _load()
+    t = np.array(lattice, dtype=np.uint8, copy=True)
+    if n_unlike0 is None:
+        n_unlike0 = n_unlike(Lx, Ly, TRI6, t, HELICAL)
+    nu = ctypes.c_int64(int(n_unlike0))
+    cnt = np.array(counters0, dtype=np.int64)
+    n_tr = n_mcs // trace_every if trace_every > 0 else 0
+    trace = np.zeros(max(n_tr, 1), dtype=np.int64)
+    rc = lib.orc_run_mpkk(Lx, Ly, float(bw), seed, _ptr(t), sweep0, n_mcs, ctypes.byref(nu), _ptr(cnt),
+                          trace_every, _ptr(trace), (1 if check else 0) | (2 if reverse else 0))
+    if rc == -2:
+        raise ValueError("the seven-site domains do not tile this helical lattice")
+    if rc != 0:
+        raise AssertionError("incremental energy disagrees with a full recount")
+    return RunResult(t, nu.value, cnt, trace[:n_tr])
 
 
 def run_random_sequential(Lx: int, Ly: int, geometry: int, bw: float, seed: int,

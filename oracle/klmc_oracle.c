@@ -41,6 +41,23 @@
  *      the order of its anchors.
  *   R7 clusters: connected components under the lattice adjacency with the same
  *      periodic wrap; histogram of component sizes, sparse and ascending.
+ *   R8 helical boundary (section "Massive Parallel Kawasaki Kinetics", Fig. 4
+ *      and its caption on helical boundary conditions): site i's neighbours are
+ *      (i + d) mod N for d in {+1, -1, +Lx, -Lx, -(Lx-1), +(Lx-1)} -- the axial
+ *      offsets of R1 read as index steps, so the x wrap continues into the next
+ *      row.  Triangular lattice only.
+ *   R9 seven-colour schedule (the MPKK loop): coverage k has the domain centres
+ *      i mod 7 = k; each centre with its six neighbours is one domain, and the
+ *      domains tile the lattice iff 7 | N and Lx mod 7 is 3 or 5.  One MCS is
+ *      seven iterations f = 0..6; iteration f of sweep s draws
+ *      w = Philox(seed, {0xFFFFFFFF, f, s_lo, s_hi}), k = floor(w0 * 7 / 2^32)
+ *      (with replacement, as the loop's k = rand%7) and one direction
+ *      d = floor(w1 * 6 / 2^32) shared by all domains; every centre c attempts
+ *      the exchange with c + D[d], draw counter {c, f, s_lo, s_hi}.  With one
+ *      shared direction no pair touches another pair (centres are three steps
+ *      apart), so the iteration does not depend on the order of its domains; a
+ *      private direction per domain, as the loop's text allows, lets the pairs of
+ *      adjacent domains neighbour each other.
  */
 #include <math.h>
 #include <stdint.h>
@@ -107,25 +124,40 @@ static int64_t site_of(int Lx, int Ly, int64_t x, int64_t y)
     return wrap(y, Ly) * (int64_t)Lx + wrap(x, Lx);
 }
 
-/* Index of the neighbour of site i in direction (dx, dy), periodic wrap. */
-static int64_t neighbour(int Lx, int Ly, int64_t i, int dx, int dy)
+#define ORC_PERIODIC 0
+#define ORC_HELICAL 1
+
+/* Index of the neighbour of site i in direction (dx, dy): periodic wrap of x and
+ * y (R1), or the helical index step dx + dy*Lx modulo N (R8). */
+static int64_t neighbour_b(int Lx, int Ly, int boundary, int64_t i, int dx, int dy)
 {
+    if (boundary == ORC_HELICAL) return wrap(i + dx + (int64_t)dy * Lx, (int64_t)Lx * Ly);
     int64_t x = i % Lx, y = i / Lx;
     return site_of(Lx, Ly, x + dx, y + dy);
+}
+
+static int64_t neighbour(int Lx, int Ly, int64_t i, int dx, int dy)
+{
+    return neighbour_b(Lx, Ly, ORC_PERIODIC, i, dx, dy);
 }
 
 /* ------------------------------------------------------------------------- */
 /* Energy (R2): number of unlike nearest-neighbour bonds, every bond once.     */
 /* ------------------------------------------------------------------------- */
-int64_t orc_n_unlike(int Lx, int Ly, int geometry, const uint8_t *t)
+int64_t orc_n_unlike_b(int Lx, int Ly, int geometry, int boundary, const uint8_t *t)
 {
     const int (*O)[2] = o_table(geometry);
     int nO = orc_n_orientations(geometry);
     int64_t N = (int64_t)Lx * Ly, n = 0;
     for (int64_t i = 0; i < N; ++i)
         for (int k = 0; k < nO; ++k)
-            n += (t[i] != t[neighbour(Lx, Ly, i, O[k][0], O[k][1])]);
+            n += (t[i] != t[neighbour_b(Lx, Ly, boundary, i, O[k][0], O[k][1])]);
     return n;
+}
+
+int64_t orc_n_unlike(int Lx, int Ly, int geometry, const uint8_t *t)
+{
+    return orc_n_unlike_b(Lx, Ly, geometry, ORC_PERIODIC, t);
 }
 
 /* ------------------------------------------------------------------------- */
@@ -250,20 +282,26 @@ int64_t orc_phase_anchors(int Lx, int Ly, int geometry, int o_index, int rx, int
 /* ------------------------------------------------------------------------- */
 
 /* Unlike bonds incident to a or b; the bond a-b itself is counted once. */
-static int local_unlike(int Lx, int Ly, int geometry, const uint8_t *t, int64_t a, int64_t b)
+static int local_unlike_b(int Lx, int Ly, int geometry, int boundary, const uint8_t *t, int64_t a,
+                          int64_t b)
 {
     const int (*NB)[2] = nb_table(geometry);
     int z = orc_coordination(geometry), n = 0;
     for (int k = 0; k < z; ++k) {
-        int64_t c = neighbour(Lx, Ly, a, NB[k][0], NB[k][1]);
+        int64_t c = neighbour_b(Lx, Ly, boundary, a, NB[k][0], NB[k][1]);
         n += (t[a] != t[c]);
     }
     for (int k = 0; k < z; ++k) {
-        int64_t c = neighbour(Lx, Ly, b, NB[k][0], NB[k][1]);
+        int64_t c = neighbour_b(Lx, Ly, boundary, b, NB[k][0], NB[k][1]);
         if (c == a) continue;
         n += (t[b] != t[c]);
     }
     return n;
+}
+
+static int local_unlike(int Lx, int Ly, int geometry, const uint8_t *t, int64_t a, int64_t b)
+{
+    return local_unlike_b(Lx, Ly, geometry, ORC_PERIODIC, t, a, b);
 }
 
 typedef struct {
@@ -284,7 +322,7 @@ static void build_table(double bw, int geometry, orc_table *tab)
         orc_threshold(bw, dn, &tab->always[dn + tab->dn_offset], &tab->thr[dn + tab->dn_offset]);
 }
 
-static void exchange_attempt(int Lx, int Ly, int geometry, const orc_table *tab,
+static void exchange_attempt(int Lx, int Ly, int geometry, int boundary, const orc_table *tab,
                              const uint32_t key[2], int64_t sweep, int phase, uint8_t *t,
                              int64_t a, int64_t b, int64_t *n_unlike, orc_counters *cnt)
 {
@@ -292,11 +330,11 @@ static void exchange_attempt(int Lx, int Ly, int geometry, const orc_table *tab,
     if (t[a] == t[b]) return; /* R4: the candidate state equals the current one */
     cnt->unlike += 1;
     /* a. candidate state x*: the lattice with a and b exchanged */
-    int before = local_unlike(Lx, Ly, geometry, t, a, b);
+    int before = local_unlike_b(Lx, Ly, geometry, boundary, t, a, b);
     uint8_t ta = t[a];
     t[a] = t[b];
     t[b] = ta;
-    int after = local_unlike(Lx, Ly, geometry, t, a, b);
+    int after = local_unlike_b(Lx, Ly, geometry, boundary, t, a, b);
     int dn = after - before;
     /* b.-c. u ~ U[0,1) from a 32-bit draw, accept iff u < min{1, exp(-bw*dn)} */
     int accept;
@@ -354,9 +392,70 @@ int orc_run(int Lx, int Ly, int geometry, double bw, uint64_t seed, uint8_t *t, 
                     int64_t ax = (int64_t)rx + (int64_t)px * k, ay = (int64_t)ry + (int64_t)py * m;
                     int64_t a = site_of(Lx, Ly, ax, ay);
                     int64_t b = site_of(Lx, Ly, ax + ox, ay + oy);
-                    exchange_attempt(Lx, Ly, geometry, &tab, key, s, f, t, a, b, n_unlike, &cnt);
+                    exchange_attempt(Lx, Ly, geometry, ORC_PERIODIC, &tab, key, s, f, t, a, b, n_unlike,
+                                     &cnt);
                 }
             if ((flags & 1) && *n_unlike != orc_n_unlike(Lx, Ly, geometry, t)) return -1;
+        }
+        int64_t done = s + 1 - sweep0;
+        if (trace_every > 0 && done % trace_every == 0) trace[done / trace_every - 1] = *n_unlike;
+    }
+    counters[0] = cnt.attempts;
+    counters[1] = cnt.unlike;
+    counters[2] = cnt.draws;
+    counters[3] = cnt.accepts;
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Helical lattice with the seven-colour schedule (R8, R9).                   */
+/* ------------------------------------------------------------------------- */
+
+/* Whether the seven coverages tile the helical Lx x Ly lattice (R9). */
+int orc_helical_valid(int Lx, int Ly)
+{
+    int64_t N = (int64_t)Lx * Ly;
+    return Lx >= 4 && Ly >= 4 && N % 7 == 0 && (Lx % 7 == 3 || Lx % 7 == 5);
+}
+
+/* Coverage k and shared direction index d of iteration f of sweep s. */
+void orc_mpkk_params(uint64_t seed, int64_t sweep, int phase, int *k, int *d)
+{
+    uint32_t key[2], w[4];
+    uint32_t ctr[4] = {0xFFFFFFFFu, (uint32_t)phase, (uint32_t)(uint64_t)sweep,
+                       (uint32_t)((uint64_t)sweep >> 32)};
+    seed_key(seed, key);
+    orc_philox4x32_10(ctr, key, w);
+    *k = (int)(((uint64_t)w[0] * 7u) >> 32);
+    *d = (int)(((uint64_t)w[1] * 6u) >> 32);
+}
+
+/* Sweeps of the seven-colour schedule on the helical triangular lattice, same
+ * arguments and flags as orc_run.  Returns -2 for a size the coverages do not
+ * tile. */
+int orc_run_mpkk(int Lx, int Ly, double bw, uint64_t seed, uint8_t *t, int64_t sweep0, int64_t n_mcs,
+                 int64_t *n_unlike, int64_t counters[4], int64_t trace_every, int64_t *trace, int flags)
+{
+    if (!orc_helical_valid(Lx, Ly)) return -2;
+    const int64_t N = (int64_t)Lx * Ly;
+    orc_table tab;
+    uint32_t key[2];
+    orc_counters cnt = {counters[0], counters[1], counters[2], counters[3]};
+    build_table(bw, ORC_TRI6, &tab);
+    seed_key(seed, key);
+    for (int64_t s = sweep0; s < sweep0 + n_mcs; ++s) {
+        for (int f = 0; f < 7; ++f) {
+            int k, d;
+            orc_mpkk_params(seed, s, f, &k, &d);
+            const int dx = TRI6_NB[d][0], dy = TRI6_NB[d][1];
+            const int64_t n_centres = N / 7;
+            for (int64_t q = 0; q < n_centres; ++q) {
+                int64_t m = (flags & 2) ? n_centres - 1 - q : q;
+                int64_t c = (int64_t)k + 7 * m;
+                int64_t b = neighbour_b(Lx, Ly, ORC_HELICAL, c, dx, dy);
+                exchange_attempt(Lx, Ly, ORC_TRI6, ORC_HELICAL, &tab, key, s, f, t, c, b, n_unlike, &cnt);
+            }
+            if ((flags & 1) && *n_unlike != orc_n_unlike_b(Lx, Ly, ORC_TRI6, ORC_HELICAL, t)) return -1;
         }
         int64_t done = s + 1 - sweep0;
         if (trace_every > 0 && done % trace_every == 0) trace[done / trace_every - 1] = *n_unlike;
@@ -376,8 +475,8 @@ int orc_run(int Lx, int Ly, int geometry, double bw, uint64_t seed, uint8_t *t, 
  * Breadth-first search started from sites in ascending order, so the first site
  * reached of every component is its smallest index.  Returns the number of
  * components. */
-int64_t orc_cluster_labels(int Lx, int Ly, int geometry, const uint8_t *t, int species,
-                           int64_t *labels)
+int64_t orc_cluster_labels_b(int Lx, int Ly, int geometry, int boundary, const uint8_t *t, int species,
+                             int64_t *labels)
 {
     const int (*NB)[2] = nb_table(geometry);
     int z = orc_coordination(geometry);
@@ -393,7 +492,7 @@ int64_t orc_cluster_labels(int Lx, int Ly, int geometry, const uint8_t *t, int s
         while (head < tail) {
             int64_t c = queue[head++];
             for (int k = 0; k < z; ++k) {
-                int64_t d = neighbour(Lx, Ly, c, NB[k][0], NB[k][1]);
+                int64_t d = neighbour_b(Lx, Ly, boundary, c, NB[k][0], NB[k][1]);
                 if (t[d] == species && labels[d] == -1) {
                     labels[d] = i;
                     queue[tail++] = d;
@@ -406,11 +505,16 @@ int64_t orc_cluster_labels(int Lx, int Ly, int geometry, const uint8_t *t, int s
     return n_comp;
 }
 
+int64_t orc_cluster_labels(int Lx, int Ly, int geometry, const uint8_t *t, int species, int64_t *labels)
+{
+    return orc_cluster_labels_b(Lx, Ly, geometry, ORC_PERIODIC, t, species, labels);
+}
+
 /* Sparse cluster-size histogram, ascending in size.  Writes at most capacity
  * (size, count) pairs and returns the number of distinct sizes (which may
  * exceed capacity), or -1 on allocation failure. */
-int64_t orc_cluster_histogram(int Lx, int Ly, int geometry, const uint8_t *t, int species,
-                              int64_t *sizes, int64_t *counts, int64_t capacity)
+int64_t orc_cluster_histogram_b(int Lx, int Ly, int geometry, int boundary, const uint8_t *t, int species,
+                                int64_t *sizes, int64_t *counts, int64_t capacity)
 {
     int64_t N = (int64_t)Lx * Ly;
     int64_t *labels = (int64_t *)malloc((size_t)N * sizeof(int64_t));
@@ -420,7 +524,7 @@ int64_t orc_cluster_histogram(int Lx, int Ly, int geometry, const uint8_t *t, in
         free(labels); free(comp_size); free(hist);
         return -1;
     }
-    orc_cluster_labels(Lx, Ly, geometry, t, species, labels);
+    orc_cluster_labels_b(Lx, Ly, geometry, boundary, t, species, labels);
     for (int64_t i = 0; i < N; ++i)
         if (labels[i] >= 0) comp_size[labels[i]] += 1;
     for (int64_t i = 0; i < N; ++i)
@@ -436,6 +540,12 @@ int64_t orc_cluster_histogram(int Lx, int Ly, int geometry, const uint8_t *t, in
         }
     free(labels); free(comp_size); free(hist);
     return n;
+}
+
+int64_t orc_cluster_histogram(int Lx, int Ly, int geometry, const uint8_t *t, int species,
+                              int64_t *sizes, int64_t *counts, int64_t capacity)
+{
+    return orc_cluster_histogram_b(Lx, Ly, geometry, ORC_PERIODIC, t, species, sizes, counts, capacity);
 }
 
 /* ------------------------------------------------------------------------- */
