@@ -45,7 +45,7 @@ typedef enum klmc_status {
 } klmc_status;
 
 enum { KLMC_TRI6 = 0, KLMC_SQ4 = 1 };                 /* geometry  */
-enum { KLMC_PERIODIC = 0 };                           /* boundary  */
+enum { KLMC_PERIODIC = 0, KLMC_HELICAL = 1 };        /* boundary  */
 enum { KLMC_PACK_AUTO = 0, KLMC_PACK_BIT = 1, KLMC_PACK_BYTE = 2 }; /* device store */
 
 /* Caller-supplied device allocator (e.g. a framework's caching allocator).
@@ -58,7 +58,19 @@ typedef void (*klmc_free_fn)(void *ptr, size_t bytes, void *stream, void *user);
 typedef struct klmc_params {
     int32_t Lx, Ly;        /* lattice sides, each >= 4; Lx*Ly <= 2^31 - 1        */
     int32_t geometry;      /* KLMC_TRI6 (the paper's lattice) or KLMC_SQ4        */
-    int32_t boundary;      /* KLMC_PERIODIC                                      */
+    int32_t boundary;      /* KLMC_PERIODIC (conflict-free shifted sublattice
+                              phases, 8 per step), or KLMC_HELICAL: the paper's
+                              helical triangular lattice (section "Massive
+                              Parallel Kawasaki Kinetics", Fig. 4) with its
+                              seven-colour MPKK schedule -- neighbours of site i
+                              are (i + dx + dy*Lx) mod N for the six axial steps;
+                              the domains (a site i with i mod 7 = k and its six
+                              neighbours) tile the lattice, which requires TRI6,
+                              7 | Lx*Ly and Lx mod 7 in {3, 5} (else EINVAL);
+                              each step is 7 iterations, each drawing k in 0..6
+                              and one direction for all domains; one launch per
+                              iteration over the device store (cluster and threads
+                              must be 0); not in batches or the server           */
     int32_t packing;       /* device store: KLMC_PACK_BIT (1 bit/site), _BYTE, or
                               _AUTO (= BIT)                                       */
     int32_t cluster;       /* CTAs that share one lattice in the resident sweep

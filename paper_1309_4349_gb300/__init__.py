@@ -17,7 +17,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libklmc.so")
 
 TRI6, SQ4 = 0, 1
-PERIODIC = 0
+PERIODIC, HELICAL = 0, 1
 PACK_AUTO, PACK_BIT, PACK_BYTE = 0, 1, 2
 
 STATUS = {0: "KLMC_OK", 1: "KLMC_EINVAL", 2: "KLMC_ENOMEM", 3: "KLMC_ECUDA", 4: "KLMC_ETIMEOUT",
@@ -184,7 +184,7 @@ class _TorchAllocator:
 
 def make_params(Lx: int, Ly: int | None = None, *, geometry: int = TRI6, packing: int = PACK_BIT,
                 n_A: int = -1, fraction_A: float = 0.5, omega_over_kT: float = 0.0, seed: int = 1,
-                cluster: int = 0, threads: int = 0, stream: int | None = None,
+                cluster: int = 0, threads: int = 0, boundary: int = 0, stream: int | None = None,
                 allocator: _TorchAllocator | None = None) -> Params:
     p = Params()
     _check(lib().klmc_params_default(ctypes.byref(p)))
@@ -198,6 +198,7 @@ def make_params(Lx: int, Ly: int | None = None, *, geometry: int = TRI6, packing
     p.seed = int(seed)
     p.cluster = int(cluster)
     p.threads = int(threads)
+    p.boundary = int(boundary)
     p.stream = stream
     if allocator is not None:
         p.alloc = allocator.alloc
@@ -211,7 +212,8 @@ class Lattice:
     def __init__(self, Lx: int, Ly: int | None = None, *, geometry: int = TRI6,
                  packing: int = PACK_BIT, n_A: int = -1, fraction_A: float = 0.5,
                  omega_over_kT: float = 0.0, seed: int = 1, cluster: int = 0, threads: int = 0,
-                 stream=None, torch_allocator: bool = True, _handle=None, _owner=None):
+                 boundary: int = 0, stream=None, torch_allocator: bool = True, _handle=None,
+                 _owner=None):
         import torch
 
         self._owner = _owner
@@ -223,8 +225,8 @@ class Lattice:
             self._alloc = _TorchAllocator(dev) if torch_allocator else None
             p = make_params(Lx, Ly, geometry=geometry, packing=packing, n_A=n_A,
                             fraction_A=fraction_A, omega_over_kT=omega_over_kT, seed=seed,
-                            cluster=cluster, threads=threads, stream=_torch_stream_handle(stream),
-                            allocator=self._alloc)
+                            cluster=cluster, threads=threads, boundary=boundary,
+                            stream=_torch_stream_handle(stream), allocator=self._alloc)
             h = ctypes.c_void_p()
             _check(lib().klmc_create_ex(ctypes.byref(h), ctypes.byref(p)))
             self._h = h

@@ -103,7 +103,17 @@ klmc_status validate(const klmc_params *p)
     const long long N = (long long)p->Lx * p->Ly;
     if (N > 2147483647LL) return fail(KLMC_EINVAL, "Lx*Ly must be <= 2^31 - 1");
     if (p->geometry != KLMC_TRI6 && p->geometry != KLMC_SQ4) return fail(KLMC_EINVAL, "unknown geometry");
-    if (p->boundary != KLMC_PERIODIC) return fail(KLMC_EINVAL, "only periodic boundaries are supported");
+    if (p->boundary != KLMC_PERIODIC && p->boundary != KLMC_HELICAL) return fail(KLMC_EINVAL, "unknown boundary");
+    if (p->boundary == KLMC_HELICAL) {
+        if (p->geometry != KLMC_TRI6)
+            return fail(KLMC_EINVAL, "helical boundaries are for the triangular lattice (seven-site domains)");
+        if (!helical_tiles(p->Lx, p->Ly))
+            return fail(KLMC_EINVAL, "helical lattice: seven-site domains tile it only when 7 divides Lx*Ly "
+                                     "and Lx mod 7 is 3 or 5");
+        if (p->cluster > 0 || p->threads != 0)
+            return fail(KLMC_EINVAL, "helical lattices run one launch per iteration; cluster and threads "
+                                     "must be 0 (or cluster -1)");
+    }
     if (p->packing != KLMC_PACK_AUTO && p->packing != KLMC_PACK_BIT && p->packing != KLMC_PACK_BYTE)
         return fail(KLMC_EINVAL, "unknown packing");
     if (!isfinite(p->omega_over_kT)) return fail(KLMC_EINVAL, "omega_over_kT must be finite");
@@ -203,15 +213,22 @@ klmc_status create_one(klmc_ctx **out, const klmc_params *p, klmc_batch *owner, 
     c->N = (long long)p->Lx * p->Ly;
     c->nA = p->n_A >= 0 ? p->n_A : (long long)floor(p->fraction_A * (double)c->N + 0.5);
     c->W = (p->Lx + 31) / 32;
-    c->cluster = p->cluster != 0 ? p->cluster : auto_cluster(p->Lx, p->Ly);
-    if (p->cluster == 0 &&
-        resident_smem_bytes(p->Lx, p->Ly, c->cluster) > (size_t)resident_max_smem_bytes())
-        c->cluster = -1;  // automatic choice, too large for shared memory: tiled path
-    c->threads = resident_default_threads(c->cluster);
-    if (p->cluster == 0 && p->threads == 0)
-        tuned_shape(p->Lx, p->Ly, p->geometry, c->p.packing, &c->cluster, &c->threads);
-    c->auto_shape = p->cluster == 0 && p->threads == 0;
-    if (p->threads != 0) c->threads = p->threads;
+    c->helical = p->boundary == KLMC_HELICAL;
+    if (c->helical) {
+        c->cluster = -1;  // one launch per iteration over the device store
+        c->threads = 256;
+        c->auto_shape = false;
+    } else {
+        c->cluster = p->cluster != 0 ? p->cluster : auto_cluster(p->Lx, p->Ly);
+        if (p->cluster == 0 &&
+            resident_smem_bytes(p->Lx, p->Ly, c->cluster) > (size_t)resident_max_smem_bytes())
+            c->cluster = -1;  // automatic choice, too large for shared memory: tiled path
+        c->threads = resident_default_threads(c->cluster);
+        if (p->cluster == 0 && p->threads == 0)
+            tuned_shape(p->Lx, p->Ly, p->geometry, c->p.packing, &c->cluster, &c->threads);
+        c->auto_shape = p->cluster == 0 && p->threads == 0;
+        if (p->threads != 0) c->threads = p->threads;
+    }
     if (c->p.packing == KLMC_PACK_BIT) {
         c->pitch = (c->W + 3) / 4 * 4;  // 16-byte rows
         c->lat_bytes = (size_t)c->pitch * 4 * p->Ly;
@@ -253,7 +270,7 @@ klmc_status create_one(klmc_ctx **out, const klmc_params *p, klmc_batch *owner, 
                                 c->init_scratch, c->stream);
     if (e == cudaSuccess)
         e = launch_recount(c->lat, J.packing, p->Lx, p->Ly, c->pitch, p->geometry,
-                           c->state + kNUnlike, c->stream);
+                           c->state + kNUnlike, c->stream, c->helical);
     if (e == cudaSuccess && sync) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {
         free_all(c);
@@ -274,13 +291,19 @@ klmc_status check_resident(const klmc_ctx *c, int cluster)
     return KLMC_OK;
 }
 
-// Tiled-path plan of the handle, and the second store buffer it needs for blocks.
+// Plan of the handle's per-launch path (tiled bands, or the seven iteration launches
+// of a helical lattice), and the second store buffer that band blocks need.
 klmc_status ensure_tiled(klmc_ctx *c)
 {
     if (c->tiled.H != 0) return KLMC_OK;
     int dev = 0, sms = 0;
     KLMC_CUDA(cudaGetDevice(&dev));
     KLMC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    c->sm_count = sms;
+    if (c->helical) {
+        c->tiled = TiledPlan{1, 1, 256, 0};
+        return KLMC_OK;
+    }
     KLMC_CUDA(configure_tiled());
     const TiledPlan plan = tiled_plan(c->p.Lx, c->p.Ly, sms);
     if (plan.K >= 2) {
@@ -289,6 +312,13 @@ klmc_status ensure_tiled(klmc_ctx *c)
     }
     c->tiled = plan;
     return KLMC_OK;
+}
+
+// Sweeps k0 .. k0+n-1 of the handle's per-launch path on job J's store.
+cudaError_t path_sweeps(klmc_ctx *c, const SweepJob &J, int k0, int n, cudaStream_t stream)
+{
+    if (c->helical) return launch_mpkk_phases(J, k0, n, c->sm_count, stream);
+    return launch_tiled_phases(J, c->tiled, c->tiled_alt, c->lat_bytes, k0, n, stream);
 }
 
 // Instantiated graph of K sweeps on the tiled path (their phase launches, then
@@ -304,7 +334,7 @@ klmc_status tiled_graph(klmc_ctx *c, int K, cudaGraphExec_t *out)
         KLMC_CUDA(cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking));
     cudaGraph_t graph = nullptr;
     KLMC_CUDA(cudaStreamBeginCapture(c->capture_stream, cudaStreamCaptureModeThreadLocal));
-    cudaError_t e = launch_tiled_phases(c->job, c->tiled, c->tiled_alt, c->lat_bytes, 0, K, c->capture_stream);
+    cudaError_t e = path_sweeps(c, c->job, 0, K, c->capture_stream);
     if (e == cudaSuccess) e = launch_advance(c->state, K, c->capture_stream);
     cudaError_t e2 = cudaStreamEndCapture(c->capture_stream, &graph);
     if (e == cudaSuccess) e = e2;
@@ -340,7 +370,7 @@ klmc_status sweep_tiled(klmc_ctx *c, int64_t n_mcs, int64_t trace_every, int64_t
         }
         if (upto > done) {
             const int r = (int)(upto - done);
-            KLMC_CUDA(launch_tiled_phases(c->job, c->tiled, c->tiled_alt, c->lat_bytes, 0, r, c->stream));
+            KLMC_CUDA(path_sweeps(c, c->job, 0, r, c->stream));
             KLMC_CUDA(launch_advance(c->state, r, c->stream));
             done = upto;
         }
@@ -429,7 +459,7 @@ klmc_status probe_shape(klmc_ctx *c, void *scratch_lat, long long *scratch_state
                                   cudaMemcpyHostToDevice, c->stream));
         KLMC_CUDA(cudaEventRecord(e0, c->stream));
         if (cluster < 0) {
-            KLMC_CUDA(launch_tiled_phases(J, c->tiled, c->tiled_alt, c->lat_bytes, 0, n, c->stream));
+            KLMC_CUDA(path_sweeps(c, J, 0, n, c->stream));
             KLMC_CUDA(launch_advance(scratch_state, n, c->stream));
         } else {
             SweepCall call;
@@ -453,6 +483,7 @@ klmc_status probe_shape(klmc_ctx *c, void *scratch_lat, long long *scratch_state
 
 klmc_status autotune(klmc_ctx *c, int probe_sweeps)
 {
+    if (c->helical) return KLMC_OK;  // one launch shape: the iteration launches
     const TuneKey key{c->p.Lx, c->p.Ly, c->p.geometry, c->job.packing};
     {
         std::lock_guard<std::mutex> lock(g_tune_mutex);
@@ -624,7 +655,7 @@ klmc_status klmc_energy_recount(klmc_ctx *c, int64_t *n_unlike)
 {
     if (!c || !n_unlike) return fail(KLMC_EINVAL, "NULL argument");
     KLMC_CUDA(launch_recount(c->lat, c->job.packing, c->p.Lx, c->p.Ly, c->pitch, c->p.geometry,
-                             c->state + kScratch0, c->stream));
+                             c->state + kScratch0, c->stream, c->helical));
     long long v = 0;
     KLMC_CUDA(cudaMemcpyAsync(&v, c->state + kScratch0, sizeof(v), cudaMemcpyDeviceToHost, c->stream));
     KLMC_CUDA(cudaStreamSynchronize(c->stream));
@@ -645,7 +676,7 @@ klmc_status klmc_cluster_histogram_device(klmc_ctx *c, int32_t species, int64_t 
     KLMC_CUDA(launch_cluster_histogram(c->lat, c->job.packing, c->p.Lx, c->p.Ly, c->pitch,
                                        c->p.geometry, species, c->cs, (long long *)dev_sizes,
                                        (long long *)dev_counts, capacity,
-                                       (long long *)dev_n_distinct, c->stream));
+                                       (long long *)dev_n_distinct, c->stream, c->helical));
     return KLMC_OK;
 }
 
@@ -717,7 +748,7 @@ klmc_status klmc_set_lattice(klmc_ctx *c, const uint8_t *host_in, int64_t n, int
     KLMC_CUDA(launch_pack(c->dbytes, c->lat, c->job.packing, c->p.Lx, c->p.Ly, c->pitch, c->stream));
     KLMC_CUDA(cudaMemsetAsync(c->state, 0, kStateSlots * sizeof(long long), c->stream));
     KLMC_CUDA(launch_recount(c->lat, c->job.packing, c->p.Lx, c->p.Ly, c->pitch, c->p.geometry,
-                             c->state + kNUnlike, c->stream));
+                             c->state + kNUnlike, c->stream, c->helical));
     KLMC_CUDA(launch_count_A(c->lat, c->job.packing, c->p.Lx, c->p.Ly, c->pitch, c->state + kScratch0,
                              c->stream));
     long long nA = 0;
@@ -738,7 +769,7 @@ klmc_status klmc_set_lattice_device(klmc_ctx *c, const uint8_t *dev_in, int64_t 
     KLMC_CUDA(launch_pack(dev_in, c->lat, c->job.packing, c->p.Lx, c->p.Ly, c->pitch, c->stream));
     KLMC_CUDA(cudaMemsetAsync(c->state, 0, kStateSlots * sizeof(long long), c->stream));
     KLMC_CUDA(launch_recount(c->lat, c->job.packing, c->p.Lx, c->p.Ly, c->pitch, c->p.geometry,
-                             c->state + kNUnlike, c->stream));
+                             c->state + kNUnlike, c->stream, c->helical));
     KLMC_CUDA(launch_count_A(c->lat, c->job.packing, c->p.Lx, c->p.Ly, c->pitch, c->state + kNA,
                              c->stream));
     c->nA_on_device = true;
@@ -790,6 +821,10 @@ klmc_status klmc_get_plan(klmc_ctx *c, int32_t *phases_per_exchange)
         *phases_per_exchange = resident_block_phases(c->p.Lx, c->p.Ly, c->cluster);
         return KLMC_OK;
     }
+    if (c->helical) {
+        *phases_per_exchange = 1;
+        return KLMC_OK;
+    }
     int dev = 0, sms = 0;
     KLMC_CUDA(cudaGetDevice(&dev));
     KLMC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -824,7 +859,9 @@ klmc_status klmc_batch_create(klmc_batch **out, const klmc_params *reps, int32_t
         p.stream = reps[0].stream;
         klmc_ctx *c = nullptr;
         klmc_status st = create_one(&c, &p, b);
-        if (st == KLMC_OK && c->cluster < 0)
+        if (st == KLMC_OK && c->helical)
+            st = fail(KLMC_EINVAL, "helical lattices run on the per-handle path, not in batches");
+        else if (st == KLMC_OK && c->cluster < 0)
             st = fail(KLMC_EINVAL, "lattice too large for a batched resident launch");
         if (st == KLMC_OK) st = check_resident(c, c->cluster);
         if (st != KLMC_OK) {

@@ -75,23 +75,26 @@ __global__ void cc_init_kernel(const void *lat, int packing, int Lx, int Ly, int
     }
 }
 
-__global__ void cc_union_kernel(int Lx, int Ly, int geometry, int32_t *parent)
+// Bonds {i, i+o}, o in (1,0), (0,1) and, for TRI6, (1,-1), with periodic wrap or
+// (helical) the x wrap carrying into the next or previous row.
+__global__ void cc_union_kernel(int Lx, int Ly, int geometry, int helical, int32_t *parent)
 {
     const long long N = (long long)Lx * Ly;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
          i += (long long)gridDim.x * blockDim.x) {
         if (parent[i] < 0) continue;
         const int y = (int)(i / Lx), x = (int)(i - (long long)y * Lx);
-        const int xp = x + 1 == Lx ? 0 : x + 1;
+        const bool xe = x + 1 == Lx;
+        const int xp = xe ? 0 : x + 1;
         const int yp = y + 1 == Ly ? 0 : y + 1;
         const int ym = y == 0 ? Ly - 1 : y - 1;
         const int self = (int)i;
-        const int j0 = y * Lx + xp;
+        const int j0 = (helical && xe ? yp : y) * Lx + xp;
         if (parent[j0] >= 0) unite(parent, self, j0);
         const int j1 = yp * Lx + x;
         if (parent[j1] >= 0) unite(parent, self, j1);
         if (geometry == kTRI6) {
-            const int j2 = ym * Lx + xp;
+            const int j2 = (helical && xe ? y : ym) * Lx + xp;
             if (parent[j2] >= 0) unite(parent, self, j2);
         }
     }
@@ -212,12 +215,12 @@ cudaError_t cluster_scratch_clear(const ClusterScratch &s, cudaStream_t stream)
 cudaError_t launch_cluster_histogram(const void *lat, int packing, int Lx, int Ly, int pitch,
                                      int geometry, int species, const ClusterScratch &s,
                                      long long *sizes, long long *counts, long long capacity,
-                                     long long *n_distinct, cudaStream_t stream)
+                                     long long *n_distinct, cudaStream_t stream, int helical)
 {
     const long long N = (long long)Lx * Ly;
     const int g = grid_for(N);
     cc_init_kernel<<<g, kBlock, 0, stream>>>(lat, packing, Lx, Ly, pitch, species, s.parent, s.csize);
-    cc_union_kernel<<<g, kBlock, 0, stream>>>(Lx, Ly, geometry, s.parent);
+    cc_union_kernel<<<g, kBlock, 0, stream>>>(Lx, Ly, geometry, helical, s.parent);
     cc_size_kernel<<<g, kBlock, 0, stream>>>(N, s.parent, s.csize);
     cc_hist_kernel<<<g, kBlock, 0, stream>>>(N, s.parent, s.csize, s.hist, s.bitmap);
     const long long nwords = (s.n_species_max + 1 + 31) / 32;

@@ -19,6 +19,7 @@ struct klmc_ctx {
     int cluster = 1;              // CTAs per lattice in the resident sweep (-1: tiled path)
     int threads = 512;            // threads per CTA of the resident sweep (128, 256 or 512)
     bool auto_shape = true;       // shape chosen by the library (params cluster = threads = 0)
+    bool helical = false;         // helical boundary, seven-colour schedule (sweep_mpkk.cu)
     size_t lat_bytes = 0;
     void *lat = nullptr;
     long long *state = nullptr;   // StateSlot array
@@ -36,6 +37,7 @@ struct klmc_ctx {
     // tiled path: band height, capture stream, and instantiated graphs of K sweeps
     klmc::TiledPlan tiled{0, 0, 0, 0};  // tiled-path plan (H = 0: not yet chosen)
     void *tiled_alt = nullptr;          // second store buffer of the blocked tiled path
+    int sm_count = 0;                   // SMs of the device (set with the tiled plan)
     cudaStream_t capture_stream = nullptr;
     std::map<int, cudaGraphExec_t> graphs;
 };

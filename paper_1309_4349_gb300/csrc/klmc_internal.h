@@ -97,6 +97,13 @@ cudaError_t launch_tiled_phases(const SweepJob &job, const TiledPlan &plan, void
 cudaError_t launch_advance(long long *state, int n, cudaStream_t stream);
 cudaError_t launch_trace(long long *state, cudaStream_t stream);
 
+// Helical triangular lattice with the seven-colour schedule (sweep_mpkk.cu): whether
+// the seven-site domains tile Lx x Ly (7 | N, Lx mod 7 in {3, 5}), and the seven
+// iteration launches of each of n_sweeps sweeps k0 .. (sweep index from
+// state[kSweepBase]).
+bool helical_tiles(int Lx, int Ly);
+cudaError_t launch_mpkk_phases(const SweepJob &job, int k0, int n_sweeps, int sm_count, cudaStream_t stream);
+
 // Initial placement: the nA sites with the smallest (64-bit Philox key, index).
 cudaError_t launch_init_lattice(void *lat, int packing, int Lx, int Ly, int pitch, uint32_t key0,
                                 uint32_t key1, long long nA, void *scratch, cudaStream_t stream);
@@ -104,7 +111,8 @@ size_t init_scratch_bytes();
 
 // n_unlike recount into *out (overwritten).
 cudaError_t launch_recount(const void *lat, int packing, int Lx, int Ly, int pitch, int geometry,
-                           long long *out, cudaStream_t stream);
+                           long long *out, cudaStream_t stream,
+                           int helical = 0);
 
 // Pack one byte per site (0/1) into the device store, and back.
 cudaError_t launch_pack(const uint8_t *bytes, void *lat, int packing, int Lx, int Ly, int pitch,
@@ -130,7 +138,8 @@ cudaError_t cluster_scratch_clear(const ClusterScratch &s, cudaStream_t stream);
 cudaError_t launch_cluster_histogram(const void *lat, int packing, int Lx, int Ly, int pitch,
                                      int geometry, int species, const ClusterScratch &s,
                                      long long *sizes, long long *counts, long long capacity,
-                                     long long *n_distinct, cudaStream_t stream);
+                                     long long *n_distinct, cudaStream_t stream,
+                                     int helical = 0);
 
 // Sets the message returned by klmc_last_error() on the calling thread.
 void set_last_error(const char *msg);

@@ -182,21 +182,24 @@ __device__ __forceinline__ void block_add(long long v, long long *out)
 
 // Unlike bonds: every site with its forward orientations (TRI6: (1,0), (0,1),
 // (1,-1); SQ4: (1,0), (0,1)), each bond once.
+// Unlike bonds {i, i+o}, o in (1,0), (0,1) and, for TRI6, (1,-1): periodic wrap of x
+// and y, or (helical) the x wrap carrying into the next or previous row.
 __global__ void recount_kernel(const void *lat, int packing, int Lx, int Ly, int pitch, int geometry,
-                               long long *out)
+                               int helical, long long *out)
 {
     long long n = 0;
     const long long N = (long long)Lx * Ly;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
          i += (long long)gridDim.x * blockDim.x) {
         const int y = (int)(i / Lx), x = (int)(i - (long long)y * Lx);
-        const int xp = x + 1 == Lx ? 0 : x + 1;
+        const bool xe = x + 1 == Lx;
+        const int xp = xe ? 0 : x + 1;
         const int yp = y + 1 == Ly ? 0 : y + 1;
         const int ym = y == 0 ? Ly - 1 : y - 1;
         const uint32_t t = site_at(lat, packing, pitch, x, y);
-        n += t != site_at(lat, packing, pitch, xp, y);
+        n += t != site_at(lat, packing, pitch, xp, helical && xe ? yp : y);
         n += t != site_at(lat, packing, pitch, x, yp);
-        if (geometry == kTRI6) n += t != site_at(lat, packing, pitch, xp, ym);
+        if (geometry == kTRI6) n += t != site_at(lat, packing, pitch, xp, helical && xe ? y : ym);
     }
     block_add(n, out);
 }
@@ -289,13 +292,13 @@ cudaError_t launch_init_lattice(void *lat, int packing, int Lx, int Ly, int pitc
 }
 
 cudaError_t launch_recount(const void *lat, int packing, int Lx, int Ly, int pitch, int geometry,
-                           long long *out, cudaStream_t stream)
+                           long long *out, cudaStream_t stream, int helical)
 {
     cudaError_t e = cudaMemsetAsync(out, 0, sizeof(long long), stream);
     if (e != cudaSuccess) return e;
     const long long N = (long long)Lx * Ly;
     recount_kernel<<<grid_for(N, kBlock * 4), kBlock, 0, stream>>>(lat, packing, Lx, Ly, pitch,
-                                                                   geometry, out);
+                                                                   geometry, helical, out);
     return cudaGetLastError();
 }
 

@@ -188,7 +188,9 @@ int admit(klmc_server *s)
             s->pending.pop_front();
         }
         klmc_status st = klmc::host::create_async(&j->ctx, &p);
-        if (st == KLMC_OK && j->ctx->cluster < 0)
+        if (st == KLMC_OK && j->ctx->helical)
+            st = fail(KLMC_EINVAL, "helical lattices run on the per-handle path, not in the server");
+        else if (st == KLMC_OK && j->ctx->cluster < 0)
             st = fail(KLMC_EINVAL, "lattice too large for the resident sweep");
         if (st != KLMC_OK) {
             if (j->ctx) klmc::host::destroy(j->ctx);

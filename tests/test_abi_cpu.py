@@ -53,7 +53,7 @@ def test_params_default(L):
 
 
 @pytest.mark.parametrize("field,value", [("Lx", 3), ("Ly", 2), ("geometry", 7), ("packing", 9),
-                                         ("boundary", 1), ("n_A", 64 * 64 + 1), ("threads", 64),
+                                         ("boundary", 1), ("boundary", 2), ("n_A", 64 * 64 + 1), ("threads", 64),
                                          ("cluster", 17), ("cluster", -2),
                                          ("omega_over_kT", float("nan")),
                                          ("omega_over_kT", float("inf"))])
@@ -65,6 +65,19 @@ def test_create_rejects_invalid(L, field, value):
     assert L.klmc_create_ex(ctypes.byref(h), ctypes.byref(p)) == 1  # KLMC_EINVAL
     assert h.value is None
     assert L.klmc_last_error().decode() != ""
+
+
+@pytest.mark.parametrize("Lx,Ly,geometry,cluster", [(10, 7, 1, 0), (11, 7, 0, 0), (10, 8, 0, 0),
+                                                     (10, 7, 0, 4)])
+def test_create_rejects_invalid_helical(L, Lx, Ly, geometry, cluster):
+    """Helical lattices need TRI6, 7 | Lx*Ly, Lx mod 7 in {3, 5} and the per-launch
+    path (no cluster)."""
+    p = klmc.Params()
+    L.klmc_params_default(ctypes.byref(p))
+    p.Lx, p.Ly, p.geometry, p.cluster, p.boundary = Lx, Ly, geometry, cluster, klmc.HELICAL
+    h = ctypes.c_void_p()
+    assert L.klmc_create_ex(ctypes.byref(h), ctypes.byref(p)) == 1
+    assert "helical" in L.klmc_last_error().decode()
 
 
 def test_create_rejects_bad_fraction_and_size(L):

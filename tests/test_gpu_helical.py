@@ -1,0 +1,92 @@
+"""The helical triangular lattice with the seven-colour MPKK schedule on the GPU
+(section "Massive Parallel Kawasaki Kinetics": seven-lipid domains covering the
+lattice under helical boundary conditions, one Kawasaki attempt per domain per
+iteration, seven iterations per step) against the oracle, bit for bit."""
+import numpy as np
+import pytest
+
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_1309_4349_gb300 as klmc  # noqa: E402
+
+klmc.build()
+
+
+def make(Lx, Ly, nA, bw, seed, packing=klmc.PACK_BIT):
+    return klmc.Lattice(Lx, Ly, geometry=klmc.TRI6, packing=packing, n_A=nA, omega_over_kT=bw, seed=seed,
+                        boundary=klmc.HELICAL)
+
+
+def assert_same_run(lat, ref, Lx, Ly):
+    assert np.array_equal(lat.get_lattice(), ref.lattice)
+    c = lat.counters()
+    assert (c["attempts"], c["unlike"], c["draws"], c["accepts"]) == ref.counters()
+    assert lat.energy()[0] == ref.n_unlike
+    assert lat.energy_recount() == ref.n_unlike == oracle.n_unlike(Lx, Ly, oracle.TRI6, ref.lattice,
+                                                                   oracle.HELICAL)
+
+
+@pytest.mark.parametrize("packing", [klmc.PACK_BIT, klmc.PACK_BYTE])
+@pytest.mark.parametrize("Lx,Ly,bw,n_mcs", [(10, 7, 0.9, 23), (12, 14, -0.5, 17), (17, 7, 0.0, 9),
+                                            (24, 21, 1.4, 13), (40, 35, 0.6, 11), (402, 399, 0.8, 5)])
+def test_helical_parity(packing, Lx, Ly, bw, n_mcs):
+    assert oracle.helical_valid(Lx, Ly)
+    nA, seed = Lx * Ly * 3 // 10, 11 + Lx
+    lat = make(Lx, Ly, nA, bw, seed, packing)
+    assert lat.launch_shape()[0] == -1 and lat.plan() == 1
+    t0 = lat.get_lattice()
+    assert np.array_equal(t0, oracle.init(Lx, Ly, nA, seed))
+    assert lat.energy()[0] == oracle.n_unlike(Lx, Ly, oracle.TRI6, t0, oracle.HELICAL)
+    lat.sweep(n_mcs - 4)
+    lat.sweep(4)
+    ref = oracle.run_mpkk(Lx, Ly, bw, seed, t0, 0, n_mcs)
+    assert_same_run(lat, ref, Lx, Ly)
+
+
+def test_helical_traced_and_large():
+    """A 1004 x 1001 lattice (about 10^6 sites), traced every 3 steps: the trace
+    and the final state equal the oracle's."""
+    Lx, Ly, bw, seed = 1004, 1001, 0.7, 5
+    nA = Lx * Ly // 2
+    lat = make(Lx, Ly, nA, bw, seed)
+    t0 = lat.get_lattice()
+    tr = lat.sweep_traced(9, 3)
+    torch.cuda.synchronize()
+    ref = oracle.run_mpkk(Lx, Ly, bw, seed, t0, 0, 9, trace_every=3)
+    assert tr.cpu().numpy().tolist() == ref.trace.tolist()
+    assert_same_run(lat, ref, Lx, Ly)
+
+
+def test_helical_set_lattice_and_histograms():
+    Lx, Ly = 31, 14
+    lat = make(Lx, Ly, 100, 1.1, 3)
+    t = oracle.run_mpkk(Lx, Ly, 1.1, 3, oracle.init(Lx, Ly, 180, 8), 0, 30).lattice
+    lat.set_lattice(t, 70)
+    assert lat.energy()[0] == oracle.n_unlike(Lx, Ly, oracle.TRI6, t, oracle.HELICAL)
+    for species in (0, 1):
+        s, c = lat.cluster_histogram(species)
+        rs, rc = oracle.cluster_histogram(Lx, Ly, oracle.TRI6, t, species, oracle.HELICAL)
+        assert np.array_equal(s, rs) and np.array_equal(c, rc)
+    lat.sweep(6)
+    ref = oracle.run_mpkk(Lx, Ly, 1.1, 3, t, 70, 6)
+    assert np.array_equal(lat.get_lattice(), ref.lattice)
+    assert lat.energy()[0] == ref.n_unlike
+
+
+def test_helical_rejections():
+    with pytest.raises(klmc.KlmcError) as e:
+        make(64, 64, 100, 0.5, 1)  # 64 mod 7 = 1: the domains do not tile it
+    assert e.value.status == 1
+    with pytest.raises(klmc.KlmcError):
+        klmc.Lattice(10, 7, geometry=klmc.SQ4, boundary=klmc.HELICAL)
+    with pytest.raises(klmc.KlmcError):
+        klmc.Lattice(10, 7, boundary=klmc.HELICAL, cluster=2)
+    with pytest.raises(klmc.KlmcError) as e:
+        klmc.Batch([dict(Lx=10, Ly=7, boundary=klmc.HELICAL)])
+    assert e.value.status == 1
