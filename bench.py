@@ -93,9 +93,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--mcs", type=int, default=N_MCS, help="steps per run (default: the workload's)")
-    ap.add_argument("--workload", choices=["c2", "c1", "c3", "c4", "c5"], default="c2",
+    ap.add_argument("--workload", choices=["c2", "c1", "c3", "c4", "c5", "c6"], default="c2",
                     help="c2 (default): 400x400 x 5 omega; c1: 64x64; c3: 8192x8192; c4: 256 replicas; "
-                         "c5: serving")
+                         "c5: serving; c6: helical 402x399 x 5 omega, seven-colour schedule")
     ap.add_argument("--jobs", type=int, default=300, help="c5: number of jobs")
     ap.add_argument("--rate", type=float, default=0.0, help="c5: arrivals per second (0: 0.8 load)")
     ap.add_argument("--skip-plain", action="store_true")
@@ -251,6 +251,10 @@ def run_reference(args, rank, world=1):
 # ---------------------------------------------------------------------------
 C1 = dict(L=64, n_A=2048, omega=0.6, seed=1, mcs=1000, hist_every=100)
 C3 = dict(L=8192, omega=0.85, seed=7, mcs=1000, trace_every=10)
+# Helical triangular lattice with the seven-colour MPKK schedule: the nearest size to
+# 400 x 400 that seven-site domains tile (7 | 402*399, 402 mod 7 = 3), the 400x400
+# workload's composition, omegas and seeds, 2000 MCS (bounded run), histograms every 500.
+C6 = dict(Lx=402, Ly=399, mcs=2000, hist_every=500)
 C4 = dict(n=256, L_min=100, L_max=1024, f_min=0.1, f_max=0.5, w_min=0.1, w_max=1.2, mcs=5000,
           seed0=1000, draw_seed=20260)
 C5 = dict(L_min=64, L_max=2048, f_min=0.1, f_max=0.5, w_min=0.1, w_max=1.2, mcs_min=1e3, mcs_max=1e5,
@@ -462,6 +466,82 @@ def bench_other(args, klmc, torch, np):
                                   "9 halo rows per side, launches replayed from a CUDA graph of 10 MCS",
                           "l2": "lattice (8 MiB) fits L2; flushed between steps"}
         line["gpu_launches"] = args.steps * (3 + 8 // K * c["mcs"] + 2 * c["mcs"] // c["trace_every"])
+    elif args.workload == "c6":
+        c = C6
+        Lx, Ly = c["Lx"], c["Ly"]
+        streams = [torch.cuda.Stream() for _ in OMEGAS]
+        lats = [klmc.Lattice(Lx, Ly, fraction_A=FRACTION_A, omega_over_kT=w, seed=sd, boundary=klmc.HELICAL,
+                             stream=st) for w, sd, st in zip(OMEGAS, SEEDS, streams)]
+        inits = [torch.from_numpy(l.get_lattice()).cuda() for l in lats]
+        nseg = c["mcs"] // c["hist_every"]
+        cap = int(np.sqrt(2.0 * Lx * Ly)) + 2
+        sz = torch.zeros((len(lats), nseg, cap), dtype=torch.int64, device="cuda")
+        ct = torch.zeros_like(sz)
+        nd = torch.zeros((len(lats), nseg), dtype=torch.int64, device="cuda")
+        torch.cuda.synchronize()
+
+        def step():
+            fork = torch.cuda.Event()
+            fork.record(stream)
+            for i, (l, st) in enumerate(zip(lats, streams)):
+                st.wait_event(fork)
+                l.set_lattice_device(inits[i], 0)
+                for k in range(nseg):
+                    l.sweep(c["hist_every"])
+                    l.cluster_histogram_device(1, sz[i, k], ct[i, k], nd[i, k:k + 1])
+            for st in streams:
+                done = torch.cuda.Event()
+                done.record(st)
+                stream.wait_event(done)
+
+        clocks.start()
+        ms = _time_steps(torch, stream, flush, step, args.steps, args.warmup)
+        clk = clocks.stop()
+        cnts = [l.counters() for l in lats]
+        attempts = sum(x["attempts"] for x in cnts)
+        draws = sum(x["draws"] for x in cnts)
+        assert attempts == len(lats) * c["mcs"] * Lx * Ly
+        ms_step = sum(ms) / len(ms)
+        cpu = None
+        if not args.skip_cpu:
+            import oracle
+            import threading as _th
+
+            oracle.build()
+            n_cpu = 60
+            oinits = [oracle.init(Lx, Ly, oracle.n_A(Lx, Ly, -1, FRACTION_A), sd) for sd in SEEDS]
+            res = [0] * len(SEEDS)
+
+            def work(i):
+                r = oracle.run_mpkk(Lx, Ly, OMEGAS[i], SEEDS[i], oinits[i], 0, n_cpu)
+                oracle.cluster_histogram(Lx, Ly, oracle.TRI6, r.lattice, 1, oracle.HELICAL)
+                res[i] = r.attempts
+
+            t0 = time.perf_counter()
+            ths = [_th.Thread(target=work, args=(i,)) for i in range(len(SEEDS))]
+            for t in ths:
+                t.start()
+            for t in ths:
+                t.join()
+            dt = time.perf_counter() - t0
+            cpu = {"value": sum(res) / dt, "unit": "attempts/s", "cores": len(SEEDS), "kind": "oracle",
+                   "sample": f"{n_cpu} MCS of each of the 5 runs plus one A-cluster histogram each, one host "
+                             f"thread per run; nproc={os.cpu_count()}"}
+        line.update({"value": attempts / (ms_step * 1e-3), "ms_per_step": ms_step,
+                     "config": {"workload": "helical triangular 402x399 (7 | N, 402 mod 7 = 3), seven-colour "
+                                            "MPKK schedule, 30% A random start, omega/kT in "
+                                            "{0.2,0.4,0.6,0.8,1.0} (5 runs, seeds 2..6), 2000 MCS each, "
+                                            "A-cluster histogram every 500 MCS, 1 bit/site",
+                                "form": "one launch per iteration (7 per MCS), a thread per domain centre, "
+                                        "graph replays; the 5 lattices on 5 streams",
+                                "l2": "flushed between steps"},
+                     "roofline": _roofline("mpkk_phase_kernel", ms_step, attempts, draws / attempts, sm_count,
+                                           clk["sm_mhz"] if clk else 2070.0, -1,
+                                           {"note": "all launches of a step, the 5 lattices' overlapping on 5 "
+                                                    "streams: time = step time"}),
+                     "cpu_baseline": cpu, "clocks": clk,
+                     "gpu_launches": args.steps * len(lats) * (3 + 7 * c["mcs"] + c["mcs"] // 8 +
+                                                               nseg * LAUNCHES_HISTOGRAM)})
     elif args.workload == "c4":
         reps = c4_replicas()
         b = klmc.Batch([dict(r, packing=klmc.PACK_BIT) for r in reps])
