@@ -98,6 +98,8 @@ def _load():
     lib.orc_cluster_labels_b.restype = i64
     lib.orc_cluster_histogram_b.argtypes = [i32, i32, i32, i32, vp, ctypes.c_int, vp, vp, i64]
     lib.orc_cluster_histogram_b.restype = i64
+    lib.orc_ffn_count.argtypes = [i32, i32, i32, i32, vp, u64, i64]
+    lib.orc_ffn_count.restype = i64
     _lib = lib
     return lib
 
@@ -282,3 +284,21 @@ def run_random_sequential(Lx: int, Ly: int, geometry: int, bw: float, seed: int,
     _load().orc_run_random_sequential(Lx, Ly, geometry, float(bw), seed, _ptr(t), attempt0,
                                       n_attempts, ctypes.byref(nu), ctypes.byref(acc))
     return t, int(nu.value), int(acc.value)
+
+
+# ---------------------------------------------------------------------------
+# Fraction of first neighbours (section "Image analysis": for every site one
+# randomly chosen nearest neighbour; similar pairs divided by the lattice size).
+# ---------------------------------------------------------------------------
+def ffn_count(Lx: int, Ly: int, geometry: int, t: np.ndarray, seed: int, sample: int,
+              boundary: int = PERIODIC) -> int:
+    """Sites whose randomly chosen nearest neighbour (sample `sample`) has the same type."""
+    t = np.ascontiguousarray(t, dtype=np.uint8)
+    return int(_load().orc_ffn_count(Lx, Ly, geometry, boundary, _ptr(t), seed, sample))
+
+
+def ffn_exact(Lx: int, Ly: int, geometry: int, t: np.ndarray, boundary: int = PERIODIC) -> float:
+    """The all-bond fraction of like neighbours, 1 - n_unlike / B, B = z N / 2: the
+    random-neighbour estimator's expectation."""
+    B = COORDINATION[geometry] * Lx * Ly // 2
+    return 1.0 - n_unlike(Lx, Ly, geometry, t, boundary) / B

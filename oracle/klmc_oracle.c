@@ -58,6 +58,12 @@
  *      apart), so the iteration does not depend on the order of its domains; a
  *      private direction per domain, as the loop's text allows, lets the pairs of
  *      adjacent domains neighbour each other.
+ *   R12 fraction of first neighbours (section "Image analysis"): for every site
+ *      one randomly chosen nearest neighbour; the count of sites whose chosen
+ *      neighbour has the same type, divided by N.  In sample m the neighbour of
+ *      site i is NB[floor(w * z / 2^32)], w = word (i mod 4) of
+ *      Philox(seed, {i div 4, 0xFFFFFFFE, m_lo, m_hi}).  Its expectation is the
+ *      all-bond fraction 1 - n_unlike / B, B = z N / 2.
  */
 #include <math.h>
 #include <stdint.h>
@@ -465,6 +471,34 @@ int orc_run_mpkk(int Lx, int Ly, double bw, uint64_t seed, uint8_t *t, int64_t s
     counters[2] = cnt.draws;
     counters[3] = cnt.accepts;
     return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Fraction of first neighbours (R12).                                        */
+/* ------------------------------------------------------------------------- */
+
+/* Number of sites whose randomly chosen nearest neighbour (sample m) has the same
+ * type; the paper's fraction is this count divided by N. */
+int64_t orc_ffn_count(int Lx, int Ly, int geometry, int boundary, const uint8_t *t, uint64_t seed,
+                      int64_t sample)
+{
+    const int (*NB)[2] = nb_table(geometry);
+    const int z = orc_coordination(geometry);
+    const int64_t N = (int64_t)Lx * Ly;
+    uint32_t key[2], w[4];
+    seed_key(seed, key);
+    int64_t similar = 0;
+    for (int64_t i = 0; i < N; ++i) {
+        if (i % 4 == 0) {
+            uint32_t ctr[4] = {(uint32_t)(i / 4), 0xFFFFFFFEu, (uint32_t)(uint64_t)sample,
+                               (uint32_t)((uint64_t)sample >> 32)};
+            orc_philox4x32_10(ctr, key, w);
+        }
+        int k = (int)(((uint64_t)w[i % 4] * (uint64_t)z) >> 32);
+        int64_t j = neighbour_b(Lx, Ly, boundary, i, NB[k][0], NB[k][1]);
+        similar += (t[i] == t[j]);
+    }
+    return similar;
 }
 
 /* ------------------------------------------------------------------------- */
