@@ -456,6 +456,27 @@ def bench_other(args, klmc, torch, np):
                                             "8 MiB lattice and its second buffer stay in L2"})
             v = {"value": attempts / (ms_step * 1e-3), "ms_per_step": ms_step, "roofline": rl,
                  "clocks": clk, "final_n_unlike": int(trace[-1].item())}
+            if geom == klmc.TRI6:
+                # Fraction of first neighbours of the final lattice: the random-neighbour
+                # estimator over all 2^26 sites, 20 samples timed with CUDA events.
+                cnt_dev = torch.zeros(1, dtype=torch.int64, device="cuda")
+                for m in range(3):
+                    lat.ffn_device(m, cnt_dev)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for m in range(20):
+                    lat.ffn_device(100 + m, cnt_dev)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms_ffn = e0.elapsed_time(e1) / 20
+                n_sites = L * L
+                lat_bytes = n_sites // 8
+                v["ffn"] = {"kernel": "ffn_kernel", "ms_per_sample": ms_ffn,
+                            "sites_per_s": n_sites / (ms_ffn * 1e-3),
+                            "algorithmic_bytes": lat_bytes,
+                            "achieved_gbs": lat_bytes / (ms_ffn * 1e-3) / 1e9,
+                            "note": "one read of the 1-bit lattice per sample (the lattice fits L2; "
+                                    "neighbour reads hit cache); plus one Philox per 4 sites"}
             line["variants"][name] = v
             if geom == klmc.TRI6:
                 line.update({"value": v["value"], "ms_per_step": ms_step, "roofline": rl, "clocks": clk})

@@ -140,6 +140,21 @@ klmc_status klmc_energy(klmc_ctx *c, int64_t *n_unlike, double *energy_over_kT);
  * changing the running value.  Synchronises. */
 klmc_status klmc_energy_recount(klmc_ctx *c, int64_t *n_unlike);
 
+/* Fraction of first neighbours (section "Image analysis"): *similar = the number
+ * of sites whose randomly chosen nearest neighbour has the same type -- the
+ * paper's fraction is *similar / N.  Sample m chooses site i's neighbour as
+ * direction floor(w z / 2^32) of (1,0), (-1,0), (0,1), (0,-1), (1,-1), (-1,1)
+ * (the first four for SQ4), w = word (i mod 4) of Philox4x32-10(seed,
+ * {i div 4, 0xFFFFFFFE, m_lo, m_hi}), a stream of its own.  *exact = 1 - n_unlike
+ * / B (B = z N / 2 bonds): the all-bond fraction, which the estimator's
+ * expectation equals.  Synchronises.  Either output pointer may be NULL; EINVAL
+ * for sample < 0. */
+klmc_status klmc_ffn(klmc_ctx *c, int64_t sample, int64_t *similar, double *exact);
+
+/* Device-side: enqueues sample m's count into *dev_similar (one int64 of device
+ * memory) and returns without synchronising. */
+klmc_status klmc_ffn_device(klmc_ctx *c, int64_t sample, int64_t *dev_similar);
+
 /* Sparse cluster-size histogram of the given species (1 = A, 0 = B): connected
  * components under the lattice adjacency with periodic wrap (section "Cluster
  * Analysis methods").  Writes (sizes[k], counts[k]) in ascending size to host

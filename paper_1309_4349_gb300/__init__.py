@@ -123,6 +123,8 @@ def lib():
         "klmc_batch_get_launch": [vp, i32, P(i32), P(i32)],
         "klmc_batch_cluster_histogram_device": [vp, i32, vp, vp, i64, vp],
         "klmc_get_plan": [vp, P(i32)],
+        "klmc_ffn": [vp, i64, P(i64), P(ctypes.c_double)],
+        "klmc_ffn_device": [vp, i64, vp],
         "klmc_batch_destroy": [vp],
         "klmc_server_create": [P(vp), ctypes.c_size_t, vp],
         "klmc_server_submit": [vp, P(Params), i64, i64, ctypes.c_uint32, P(u64)],
@@ -280,6 +282,18 @@ class Lattice:
         _check(lib().klmc_cluster_histogram(self._h, int(species), sizes.ctypes.data,
                                             counts.ctypes.data, cap, ctypes.byref(n)))
         return sizes[:n.value].copy(), counts[:n.value].copy()
+
+    def ffn(self, sample: int = 0) -> tuple[float, float]:
+        """(random-neighbour fraction of first neighbours of sample `sample`, all-bond
+        fraction 1 - n_unlike / B)."""
+        n, e = ctypes.c_int64(), ctypes.c_double()
+        _check(lib().klmc_ffn(self._h, int(sample), ctypes.byref(n), ctypes.byref(e)))
+        return n.value / self.N, e.value
+
+    def ffn_device(self, sample: int, out):
+        """Enqueues sample `sample`'s similar-neighbour count into a one-element int64
+        CUDA tensor (no synchronisation)."""
+        _check(lib().klmc_ffn_device(self._h, int(sample), out.data_ptr()))
 
     def cluster_histogram_device(self, species, sizes, counts, n_distinct):
         """Enqueues the histogram into int64 CUDA tensors (no synchronisation)."""

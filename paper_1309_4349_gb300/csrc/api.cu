@@ -651,6 +651,35 @@ klmc_status klmc_energy(klmc_ctx *c, int64_t *n_unlike, double *energy_over_kT)
     return KLMC_OK;
 }
 
+klmc_status klmc_ffn_device(klmc_ctx *c, int64_t sample, int64_t *dev_similar)
+{
+    if (!c || !dev_similar) return fail(KLMC_EINVAL, "NULL argument");
+    if (sample < 0) return fail(KLMC_EINVAL, "sample must be >= 0");
+    KLMC_CUDA(launch_ffn(c->lat, c->job.packing, c->p.Lx, c->p.Ly, c->pitch, c->p.geometry, c->helical,
+                         c->job.key0, c->job.key1, sample, (long long *)dev_similar, c->stream));
+    return KLMC_OK;
+}
+
+klmc_status klmc_ffn(klmc_ctx *c, int64_t sample, int64_t *similar, double *exact)
+{
+    if (!c) return fail(KLMC_EINVAL, "ctx is NULL");
+    if (sample < 0) return fail(KLMC_EINVAL, "sample must be >= 0");
+    long long v[2] = {0, 0};  // n_unlike, similar
+    if (similar) {
+        klmc_status st = klmc_ffn_device(c, sample, (int64_t *)(c->state + kFfn));
+        if (st != KLMC_OK) return st;
+        KLMC_CUDA(cudaMemcpyAsync(&v[1], c->state + kFfn, sizeof(long long), cudaMemcpyDeviceToHost, c->stream));
+    }
+    KLMC_CUDA(cudaMemcpyAsync(&v[0], c->state + kNUnlike, sizeof(long long), cudaMemcpyDeviceToHost, c->stream));
+    KLMC_CUDA(cudaStreamSynchronize(c->stream));
+    if (similar) *similar = v[1];
+    if (exact) {
+        const double B = (double)(c->p.geometry == KLMC_TRI6 ? 3 : 2) * (double)c->N;
+        *exact = 1.0 - (double)v[0] / B;
+    }
+    return KLMC_OK;
+}
+
 klmc_status klmc_energy_recount(klmc_ctx *c, int64_t *n_unlike)
 {
     if (!c || !n_unlike) return fail(KLMC_EINVAL, "NULL argument");

@@ -24,6 +24,7 @@ enum StateSlot : int {
     kSweepBase = 7, // absolute sweep index read by the tiled phase kernels
     kTracePos = 8,  // next entry of the energy trace (tiled path)
     kTracePtr = 9,  // device address of the energy trace (tiled path)
+    kFfn = 10,      // random-neighbour count of klmc_ffn
     kStateSlots = 12
 };
 
@@ -96,6 +97,11 @@ cudaError_t launch_tiled_phases(const SweepJob &job, const TiledPlan &plan, void
                                 int k0, int n_sweeps, cudaStream_t stream);
 cudaError_t launch_advance(long long *state, int n, cudaStream_t stream);
 cudaError_t launch_trace(long long *state, cudaStream_t stream);
+
+// Fraction of first neighbours, random-neighbour estimator of sample `sample`: the
+// count of sites whose chosen neighbour is like them, into *out (overwritten).
+cudaError_t launch_ffn(const void *lat, int packing, int Lx, int Ly, int pitch, int geometry, int helical,
+                       uint32_t key0, uint32_t key1, long long sample, long long *out, cudaStream_t stream);
 
 // Helical triangular lattice with the seven-colour schedule (sweep_mpkk.cu): whether
 // the seven-site domains tile Lx x Ly (7 | N, Lx mod 7 in {3, 5}), and the seven

@@ -16,6 +16,29 @@ namespace {
 
 constexpr int kBlock = 256;
 
+// Philox4x32-10 (Salmon et al., SC'11), all four output words.
+__device__ __forceinline__ void philox_w4(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,
+                                          uint32_t k1, uint32_t o[4])
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        unsigned long long p0 = (unsigned long long)c0 * 0xD2511F53ull;
+        unsigned long long p1 = (unsigned long long)c2 * 0xCD9E8D57ull;
+        uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0;
+        uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1;
+        c1 = (uint32_t)p1;
+        c3 = (uint32_t)p0;
+        c0 = n0;
+        c2 = n2;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    o[0] = c0;
+    o[1] = c1;
+    o[2] = c2;
+    o[3] = c3;
+}
+
 __device__ __forceinline__ void philox_w01(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
                                            uint32_t k0, uint32_t k1, uint32_t &o0, uint32_t &o1)
 {
@@ -204,6 +227,52 @@ __global__ void recount_kernel(const void *lat, int packing, int Lx, int Ly, int
     block_add(n, out);
 }
 
+// Fraction of first neighbours, random-neighbour estimator (sample m): the number
+// of sites whose chosen nearest neighbour has the same type.  Site i's neighbour is
+// direction floor(w z / 2^32) of (1,0), (-1,0), (0,1), (0,-1), (1,-1), (-1,1) (the
+// first four for SQ4), w = word (i mod 4) of Philox(seed, {i div 4, 0xFFFFFFFE,
+// m_lo, m_hi}); periodic wrap, or the helical wrap of x into the next row.
+__constant__ int kNbX[6] = {1, -1, 0, 0, 1, -1};
+__constant__ int kNbY[6] = {0, 0, 1, -1, -1, 1};
+
+__global__ void ffn_kernel(const void *lat, int packing, int Lx, int Ly, int pitch, int geometry, int helical,
+                           uint32_t k0, uint32_t k1, unsigned long long m, long long *out)
+{
+    const uint32_t z = geometry == kTRI6 ? 6u : 4u;
+    const long long N = (long long)Lx * Ly;
+    const long long G = (N + 3) / 4;
+    long long n = 0;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < G;
+         q += (long long)gridDim.x * blockDim.x) {
+        uint32_t w[4];
+        philox_w4((uint32_t)q, 0xFFFFFFFEu, (uint32_t)m, (uint32_t)(m >> 32), k0, k1, w);
+        const long long i0 = 4 * q;
+        int y = (int)(i0 / Lx), x = (int)(i0 - (long long)y * Lx);
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            if (i0 + r < N) {
+                const int k = (int)__umulhi(w[r], z);
+                int nx = x + kNbX[k], ny = y + kNbY[k];
+                if (nx >= Lx) {
+                    nx -= Lx;
+                    if (helical) ny += 1;
+                } else if (nx < 0) {
+                    nx += Lx;
+                    if (helical) ny -= 1;
+                }
+                if (ny >= Ly) ny -= Ly;
+                if (ny < 0) ny += Ly;
+                n += site_at(lat, packing, pitch, x, y) == site_at(lat, packing, pitch, nx, ny);
+            }
+            if (++x == Lx) {
+                x = 0;
+                ++y;
+            }
+        }
+    }
+    block_add(n, out);
+}
+
 __global__ void count_A_kernel(const void *lat, int packing, int Lx, int Ly, int pitch, long long *out)
 {
     long long n = 0;
@@ -299,6 +368,17 @@ cudaError_t launch_recount(const void *lat, int packing, int Lx, int Ly, int pit
     const long long N = (long long)Lx * Ly;
     recount_kernel<<<grid_for(N, kBlock * 4), kBlock, 0, stream>>>(lat, packing, Lx, Ly, pitch,
                                                                    geometry, helical, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ffn(const void *lat, int packing, int Lx, int Ly, int pitch, int geometry, int helical,
+                       uint32_t key0, uint32_t key1, long long sample, long long *out, cudaStream_t stream)
+{
+    cudaError_t e = cudaMemsetAsync(out, 0, sizeof(long long), stream);
+    if (e != cudaSuccess) return e;
+    const long long G = ((long long)Lx * Ly + 3) / 4;
+    ffn_kernel<<<grid_for(G, kBlock * 2), kBlock, 0, stream>>>(lat, packing, Lx, Ly, pitch, geometry, helical,
+                                                              key0, key1, (unsigned long long)sample, out);
     return cudaGetLastError();
 }
 
