@@ -100,6 +100,10 @@ def _load():
     lib.orc_cluster_histogram_b.restype = i64
     lib.orc_ffn_count.argtypes = [i32, i32, i32, i32, vp, u64, i64]
     lib.orc_ffn_count.restype = i64
+    lib.orc_snapshot.argtypes = [i32, i32, vp, i32, i32, i32, vp, vp]
+    lib.orc_snapshot.restype = ctypes.c_int
+    lib.orc_image_ffn.argtypes = [vp, vp, i32, i32, i32, u64, i64, ctypes.POINTER(i64)]
+    lib.orc_image_ffn.restype = i64
     _lib = lib
     return lib
 
@@ -302,3 +306,33 @@ def ffn_exact(Lx: int, Ly: int, geometry: int, t: np.ndarray, boundary: int = PE
     random-neighbour estimator's expectation."""
     B = COORDINATION[geometry] * Lx * Ly // 2
     return 1.0 - n_unlike(Lx, Ly, geometry, t, boundary) / B
+
+
+# ---------------------------------------------------------------------------
+# Snapshot images (section "Image analysis": one pixel per site, sloped to keep
+# the triangular geometry, scaled with supersampling to gray levels) and the
+# image's fraction of first neighbours with a gray-level threshold.
+# ---------------------------------------------------------------------------
+def snapshot(Lx: int, Ly: int, t: np.ndarray, W: int, H: int, S: int):
+    """(image, mask): gray levels 0..255 and lattice membership, arrays of H x W."""
+    t = np.ascontiguousarray(t, dtype=np.uint8)
+    image = np.zeros(W * H, dtype=np.uint8)
+    mask = np.zeros(W * H, dtype=np.uint8)
+    if _load().orc_snapshot(Lx, Ly, _ptr(t), W, H, S, _ptr(image), _ptr(mask)) != 0:
+        raise ValueError("bad snapshot size")
+    return image.reshape(H, W), mask.reshape(H, W)
+
+
+def image_ffn(image: np.ndarray, mask: np.ndarray, delta: int, seed: int, sample: int):
+    """(similar pixels, lattice pixels) of one random-neighbour sample of the image."""
+    H, W = image.shape
+    im = np.ascontiguousarray(image, dtype=np.uint8)
+    mk = np.ascontiguousarray(mask, dtype=np.uint8)
+    n = ctypes.c_int64()
+    sim = _load().orc_image_ffn(_ptr(im), _ptr(mk), W, H, delta, seed, sample, ctypes.byref(n))
+    return int(sim), int(n.value)
+
+
+def natural_width(Lx: int, Ly: int) -> int:
+    """Image width of one pixel per half-site: U = 2 Lx + Ly - 1."""
+    return 2 * Lx + Ly - 1

@@ -64,6 +64,21 @@
  *      site i is NB[floor(w * z / 2^32)], w = word (i mod 4) of
  *      Philox(seed, {i div 4, 0xFFFFFFFE, m_lo, m_hi}).  Its expectation is the
  *      all-bond fraction 1 - n_unlike / B, B = z N / 2.
+ *   R13 snapshot images (section "Image analysis"): one pixel per site, row y
+ *      shifted by half a site (the slope that keeps the triangular geometry):
+ *      site (x, y) covers u in [2x + y, 2x + y + 2) half-sites and v in [y, y+1)
+ *      rows, U = 2 Lx + Ly - 1 half-sites wide.  A W x H image samples each
+ *      output pixel (i, j) on an S x S grid (supersampling): sample (a, b) sits
+ *      at u = (2(iS + a) + 1) U / (2WS), v = (2(jS + b) + 1) Ly / (2HS), row
+ *      y = floor(v), x = floor((u - y) / 2), inside iff 0 <= x < Lx; all in
+ *      integers.  The pixel belongs to the lattice iff at least half its samples
+ *      are inside; its gray level is round(255 nA / n_in) (A white, B black,
+ *      halves up).  The image's fraction of first neighbours (sample m): every
+ *      lattice pixel p = jW + i chooses one of its eight neighbours, direction
+ *      floor(w * 8 / 2^32) of (1,0), (1,1), (0,1), (-1,1), (-1,0), (-1,-1),
+ *      (0,-1), (1,-1), w = word (p mod 4) of Philox(seed, {p div 4, 0xFFFFFFFC,
+ *      m_lo, m_hi}); it is similar iff that neighbour is a lattice pixel of the
+ *      image whose gray level differs by at most delta (35 in the paper).
  */
 #include <math.h>
 #include <stdint.h>
@@ -498,6 +513,72 @@ int64_t orc_ffn_count(int Lx, int Ly, int geometry, int boundary, const uint8_t 
         int64_t j = neighbour_b(Lx, Ly, boundary, i, NB[k][0], NB[k][1]);
         similar += (t[i] == t[j]);
     }
+    return similar;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Snapshot images and their fraction of first neighbours (R13).              */
+/* ------------------------------------------------------------------------- */
+
+static int64_t floor_div64(int64_t a, int64_t b)
+{
+    int64_t q = a / b;
+    if ((a % b != 0) && ((a < 0) != (b < 0))) --q;
+    return q;
+}
+
+/* Gray level (0..255) and lattice membership (0/1) of every pixel, j-major. */
+int orc_snapshot(int Lx, int Ly, const uint8_t *t, int W, int H, int S, uint8_t *image, uint8_t *mask)
+{
+    if (W < 1 || H < 1 || S < 1 || S > 64) return -1;
+    const int64_t U = 2 * (int64_t)Lx + Ly - 1, D = 2 * (int64_t)W * S;
+    for (int j = 0; j < H; ++j)
+        for (int i = 0; i < W; ++i) {
+            int64_t n_in = 0, n_A = 0;
+            for (int b = 0; b < S; ++b) {
+                const int64_t y = (2 * ((int64_t)j * S + b) + 1) * (int64_t)Ly / (2 * (int64_t)H * S);
+                for (int a = 0; a < S; ++a) {
+                    const int64_t un = (2 * ((int64_t)i * S + a) + 1) * U;  /* u = un / D */
+                    const int64_t x = floor_div64(un - y * D, 2 * D);
+                    if (x < 0 || x >= Lx) continue;
+                    n_in += 1;
+                    n_A += t[y * Lx + x];
+                }
+            }
+            const int64_t p = (int64_t)j * W + i;
+            mask[p] = (uint8_t)(2 * n_in >= (int64_t)S * S);
+            image[p] = n_in > 0 ? (uint8_t)((510 * n_A + n_in) / (2 * n_in)) : 0;
+        }
+    return 0;
+}
+
+/* Similar pixels of sample m, and (pixels) the lattice pixels of the image. */
+int64_t orc_image_ffn(const uint8_t *image, const uint8_t *mask, int W, int H, int delta, uint64_t seed,
+                      int64_t sample, int64_t *pixels)
+{
+    static const int DI[8] = {1, 1, 0, -1, -1, -1, 0, 1};
+    static const int DJ[8] = {0, 1, 1, 1, 0, -1, -1, -1};
+    uint32_t key[2], w[4];
+    seed_key(seed, key);
+    int64_t similar = 0, n = 0;
+    const int64_t P = (int64_t)W * H;
+    for (int64_t p = 0; p < P; ++p) {
+        if (p % 4 == 0) {
+            uint32_t ctr[4] = {(uint32_t)(p / 4), 0xFFFFFFFCu, (uint32_t)(uint64_t)sample,
+                               (uint32_t)((uint64_t)sample >> 32)};
+            orc_philox4x32_10(ctr, key, w);
+        }
+        if (!mask[p]) continue;
+        n += 1;
+        const int k = (int)(((uint64_t)w[p % 4] * 8u) >> 32);
+        const int64_t i = p % W + DI[k], j = p / W + DJ[k];
+        if (i < 0 || i >= W || j < 0 || j >= H) continue;
+        const int64_t q = j * W + i;
+        if (!mask[q]) continue;
+        const int d = (int)image[p] - (int)image[q];
+        similar += (d <= delta && -d <= delta);
+    }
+    if (pixels) *pixels = n;
     return similar;
 }
 
