@@ -155,6 +155,29 @@ klmc_status klmc_ffn(klmc_ctx *c, int64_t sample, int64_t *similar, double *exac
  * memory) and returns without synchronising. */
 klmc_status klmc_ffn_device(klmc_ctx *c, int64_t sample, int64_t *dev_similar);
 
+/* Snapshot image of the lattice (section "Image analysis": one pixel per site,
+ * white A and black B, sloped to keep the triangular geometry, scaled down with
+ * supersampling).  Site (x, y) covers u in [2x + y, 2x + y + 2) half-sites and
+ * v in [y, y+1) rows; the image spans U = 2 Lx + Ly - 1 half-sites by Ly rows.
+ * Output pixel (i, j) averages an S x S grid of samples at
+ * u = (2(iS + a) + 1) U / (2WS), v = (2(jS + b) + 1) Ly / (2HS) (integer
+ * arithmetic: row floor(v), site floor((u - row) / 2), inside iff 0 <= x < Lx).
+ * dev_image[jW + i] = round(255 n_A / n_in) (0 with no sample inside),
+ * dev_mask[jW + i] = 1 iff at least half the samples are inside.  W = U, H =
+ * round(sqrt(3) Ly) keeps the geometry at one pixel per half-site.  Both
+ * buffers are W*H bytes of caller device memory.  1 <= S <= 64.  Enqueued. */
+klmc_status klmc_snapshot(klmc_ctx *c, int32_t W, int32_t H, int32_t S, uint8_t *dev_image, uint8_t *dev_mask);
+
+/* Fraction of first neighbours of a W x H gray image (section "Image analysis":
+ * every lattice pixel takes one random neighbour pixel; similar when the gray
+ * levels differ by at most delta, 35 in the paper).  Pixel p = jW + i takes
+ * direction floor(w * 8 / 2^32) of (1,0), (1,1), (0,1), (-1,1), (-1,0), (-1,-1),
+ * (0,-1), (1,-1), w = word (p mod 4) of Philox4x32-10(the handle's seed,
+ * {p div 4, 0xFFFFFFFC, m_lo, m_hi}); neighbours outside the image or the mask
+ * are not similar.  *similar / *pixels is the fraction.  Synchronises. */
+klmc_status klmc_image_ffn(klmc_ctx *c, const uint8_t *dev_image, const uint8_t *dev_mask, int32_t W, int32_t H,
+                           int32_t delta, int64_t sample, int64_t *similar, int64_t *pixels);
+
 /* Sparse cluster-size histogram of the given species (1 = A, 0 = B): connected
  * components under the lattice adjacency with periodic wrap (section "Cluster
  * Analysis methods").  Writes (sizes[k], counts[k]) in ascending size to host

@@ -532,6 +532,7 @@ int orc_snapshot(int Lx, int Ly, const uint8_t *t, int W, int H, int S, uint8_t 
 {
     if (W < 1 || H < 1 || S < 1 || S > 64) return -1;
     const int64_t U = 2 * (int64_t)Lx + Ly - 1, D = 2 * (int64_t)W * S;
+    if (2.0 * W * S * (U > Ly ? U : Ly) > 4.0e18 || 2.0 * H * S * (double)Ly > 4.0e18) return -1;
     for (int j = 0; j < H; ++j)
         for (int i = 0; i < W; ++i) {
             int64_t n_in = 0, n_A = 0;

@@ -125,6 +125,8 @@ def lib():
         "klmc_get_plan": [vp, P(i32)],
         "klmc_ffn": [vp, i64, P(i64), P(ctypes.c_double)],
         "klmc_ffn_device": [vp, i64, vp],
+        "klmc_snapshot": [vp, i32, i32, i32, vp, vp],
+        "klmc_image_ffn": [vp, vp, vp, i32, i32, i32, i64, P(i64), P(i64)],
         "klmc_batch_destroy": [vp],
         "klmc_server_create": [P(vp), ctypes.c_size_t, vp],
         "klmc_server_submit": [vp, P(Params), i64, i64, ctypes.c_uint32, P(u64)],
@@ -289,6 +291,24 @@ class Lattice:
         n, e = ctypes.c_int64(), ctypes.c_double()
         _check(lib().klmc_ffn(self._h, int(sample), ctypes.byref(n), ctypes.byref(e)))
         return n.value / self.N, e.value
+
+    def snapshot(self, W: int, H: int, S: int = 1):
+        """(image, mask) as uint8 CUDA tensors of shape (H, W): gray levels of the
+        sloped, supersampled lattice and lattice-pixel membership."""
+        import torch
+
+        image = torch.empty((H, W), dtype=torch.uint8, device="cuda")
+        mask = torch.empty((H, W), dtype=torch.uint8, device="cuda")
+        _check(lib().klmc_snapshot(self._h, int(W), int(H), int(S), image.data_ptr(), mask.data_ptr()))
+        return image, mask
+
+    def image_ffn(self, image, mask, delta: int = 35, sample: int = 0) -> tuple[int, int]:
+        """(similar pixels, lattice pixels) of one random-neighbour sample of an image."""
+        H, W = image.shape
+        sim, px = ctypes.c_int64(), ctypes.c_int64()
+        _check(lib().klmc_image_ffn(self._h, image.data_ptr(), mask.data_ptr(), int(W), int(H), int(delta),
+                                    int(sample), ctypes.byref(sim), ctypes.byref(px)))
+        return sim.value, px.value
 
     def ffn_device(self, sample: int, out):
         """Enqueues sample `sample`'s similar-neighbour count into a one-element int64

@@ -12,7 +12,7 @@ CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libklmc.so")
 SOURCES = ["sweep_resident.cu", "sweep_tiled.cu", "sweep_mpkk.cu", "lattice_ops.cu", "clusters.cu",
-           "clusters_noalloc.cu", "api.cu", "server.cu"]
+           "clusters_noalloc.cu", "images.cu", "api.cu", "server.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -680,6 +680,38 @@ klmc_status klmc_ffn(klmc_ctx *c, int64_t sample, int64_t *similar, double *exac
     return KLMC_OK;
 }
 
+klmc_status klmc_snapshot(klmc_ctx *c, int32_t W, int32_t H, int32_t S, uint8_t *dev_image, uint8_t *dev_mask)
+{
+    if (!c || !dev_image || !dev_mask) return fail(KLMC_EINVAL, "NULL argument");
+    if (W < 1 || H < 1 || S < 1 || S > 64) return fail(KLMC_EINVAL, "need W, H >= 1 and 1 <= S <= 64");
+    if ((long long)W * H > 2147483647LL) return fail(KLMC_EINVAL, "W*H must be <= 2^31 - 1");
+    {
+        // sample positions are exact in 64-bit integers: (2WS) max(U, Ly) and (2HS) Ly stay below 2^62
+        const double U = 2.0 * c->p.Lx + c->p.Ly - 1.0, m = U > c->p.Ly ? U : (double)c->p.Ly;
+        if (2.0 * W * S * m > 4.0e18 || 2.0 * H * S * (double)c->p.Ly > 4.0e18)
+            return fail(KLMC_EINVAL, "image too large for exact sample positions");
+    }
+    KLMC_CUDA(launch_snapshot(c->lat, c->job.packing, c->pitch, c->p.Lx, c->p.Ly, W, H, S, dev_image, dev_mask,
+                              c->stream));
+    return KLMC_OK;
+}
+
+klmc_status klmc_image_ffn(klmc_ctx *c, const uint8_t *dev_image, const uint8_t *dev_mask, int32_t W, int32_t H,
+                           int32_t delta, int64_t sample, int64_t *similar, int64_t *pixels)
+{
+    if (!c || !dev_image || !dev_mask) return fail(KLMC_EINVAL, "NULL argument");
+    if (W < 1 || H < 1 || (long long)W * H > 2147483647LL) return fail(KLMC_EINVAL, "bad image size");
+    if (delta < 0 || sample < 0) return fail(KLMC_EINVAL, "delta and sample must be >= 0");
+    KLMC_CUDA(launch_image_ffn(dev_image, dev_mask, W, H, delta, c->job.key0, c->job.key1, sample,
+                               c->state + kFfn, c->stream));
+    long long v[2];
+    KLMC_CUDA(cudaMemcpyAsync(v, c->state + kFfn, sizeof(v), cudaMemcpyDeviceToHost, c->stream));
+    KLMC_CUDA(cudaStreamSynchronize(c->stream));
+    if (similar) *similar = v[0];
+    if (pixels) *pixels = v[1];
+    return KLMC_OK;
+}
+
 klmc_status klmc_energy_recount(klmc_ctx *c, int64_t *n_unlike)
 {
     if (!c || !n_unlike) return fail(KLMC_EINVAL, "NULL argument");

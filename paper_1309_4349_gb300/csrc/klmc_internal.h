@@ -24,7 +24,7 @@ enum StateSlot : int {
     kSweepBase = 7, // absolute sweep index read by the tiled phase kernels
     kTracePos = 8,  // next entry of the energy trace (tiled path)
     kTracePtr = 9,  // device address of the energy trace (tiled path)
-    kFfn = 10,      // random-neighbour count of klmc_ffn
+    kFfn = 10,      // random-neighbour count of klmc_ffn; with slot 11, klmc_image_ffn's counts
     kStateSlots = 12
 };
 
@@ -102,6 +102,14 @@ cudaError_t launch_trace(long long *state, cudaStream_t stream);
 // count of sites whose chosen neighbour is like them, into *out (overwritten).
 cudaError_t launch_ffn(const void *lat, int packing, int Lx, int Ly, int pitch, int geometry, int helical,
                        uint32_t key0, uint32_t key1, long long sample, long long *out, cudaStream_t stream);
+
+// Snapshot images (images.cu): W x H gray levels and lattice-pixel mask with S x S
+// supersampling; and the image's (similar, lattice pixels) counts of sample `sample`
+// into out2[0..1] (overwritten).
+cudaError_t launch_snapshot(const void *lat, int packing, int pitch, int Lx, int Ly, int W, int H, int S,
+                            uint8_t *image, uint8_t *mask, cudaStream_t stream);
+cudaError_t launch_image_ffn(const uint8_t *image, const uint8_t *mask, int W, int H, int delta, uint32_t key0,
+                             uint32_t key1, long long sample, long long *out2, cudaStream_t stream);
 
 // Helical triangular lattice with the seven-colour schedule (sweep_mpkk.cu): whether
 // the seven-site domains tile Lx x Ly (7 | N, Lx mod 7 in {3, 5}), and the seven
