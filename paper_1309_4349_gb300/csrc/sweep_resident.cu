@@ -155,6 +155,45 @@ __device__ __forceinline__ void phase_barrier(int C)
     }
 }
 
+// Per-phase task table of a small band (at most kTabW words per row and kTabRows
+// anchor rows in the phase): the anchor mask of every word and, per task row mi,
+// the local row and the row's first site index.  The CTA's last warp builds the
+// next phase's table while the other warps run the current phase.
+constexpr int kTabW = 64;
+constexpr int kTabRows = 64;
+
+struct TaskTab {
+    uint32_t am[kTabW];
+    int2 row[kTabRows];  // (local row, y * Lx)
+};
+
+__device__ __forceinline__ bool table_fits(const Geo &g, const PhaseR &P)
+{
+    return g.W <= kTabW && P.c[3] <= kTabRows;
+}
+
+template <bool BLOCKED>
+__device__ __forceinline__ void build_task_table(const PhaseR &P, const Geo &g, TaskTab *T)
+{
+    if (!table_fits(g, P)) return;
+    const int lane = threadIdx.x & 31;
+    for (int j = lane; j < g.W; j += 32) T->am[j] = anchor_mask(j << 5, P, g.Lx);
+    for (int mi = lane; mi < P.c[3]; mi += 32) {
+        const int m = mi < P.c[0] ? P.a[0] + mi
+                    : (mi < P.c[1] ? P.a[1] + mi : (mi < P.c[2] ? P.a[2] + mi : P.a[3] + mi));
+        int y = P.ry + P.py * m;
+        if (y >= g.Ly) y -= g.Ly;
+        int lr;
+        if (BLOCKED) {
+            lr = y - g.base;
+            if (lr < 0) lr += g.Ly;
+        } else {
+            lr = y - g.Y0 + 2;
+        }
+        T->row[mi] = make_int2(lr, y * g.Lx);
+    }
+}
+
 // One phase of one band.  Every task is (anchor row, word j).  BLOCKED: the
 // anchors span the band and part of its halo, all flips are local, and only
 // anchors of the band are counted; otherwise the anchors are those of the band
@@ -163,7 +202,7 @@ template <int G, int OI, int THREADS, bool BLOCKED>
 __device__ __forceinline__ void run_phase(const uint32_t *lat, const Geo &g, const PhaseR &P,
                                           const uint64_t *thr, int f,
                                           uint32_t s_lo, uint32_t s_hi, Acc &A, uint2 *dq = nullptr,
-                                          uint32_t *wacc = nullptr)
+                                          uint32_t *wacc = nullptr, const TaskTab *tt = nullptr)
 {
     // b = a + o: (1,0) -> same row, +1; (0,1) -> next row; (1,-1) -> previous row, +1
     constexpr int bdy = OI == 0 ? 0 : (OI == 1 ? 1 : -1);
@@ -176,28 +215,37 @@ __device__ __forceinline__ void run_phase(const uint32_t *lat, const Geo &g, con
     // (At 512 threads the extra evaluations cost more issue slots than they save.)
     const int ls = THREADS > 256 ? 0 : (4 * P.ntask <= THREADS ? 2 : (2 * P.ntask <= THREADS ? 1 : 0));
     const int nlane = P.ntask << ls;
+    const bool use_tab = tt != nullptr && table_fits(g, P);
     const DrawKey dk = draw_key((uint32_t)f, s_lo, s_hi, g.k0, g.k1);
     for (int t0 = threadIdx.x & ~31; t0 < nlane; t0 += THREADS) {
         const int tl = t0 + lane;
         uint32_t am = 0u, ta = 0u, tb = 0u;
         Planes S = {0u, 0u, 0u, 0u};
-        int y = 0, x0 = 0, lr = 0;
+        int ybase = 0, x0 = 0, lr = 0;
         if (tl < nlane) {
             const int t = tl >> ls;
             const int mi = (int)(((unsigned long long)t * g.magicW) >> 32);
             const int j = t - mi * g.W;
-            const int m = mi < P.c[0] ? P.a[0] + mi
-                        : (mi < P.c[1] ? P.a[1] + mi : (mi < P.c[2] ? P.a[2] + mi : P.a[3] + mi));
-            y = P.ry + P.py * m;
-            if (y >= g.Ly) y -= g.Ly;
-            if (BLOCKED) {
-                lr = y - g.base;
-                if (lr < 0) lr += g.Ly;
-            } else {
-                lr = y - g.Y0 + 2;  // y is a band row
-            }
             x0 = j << 5;
-            am = anchor_mask(x0, P, g.Lx);
+            if (use_tab) {
+                const int2 r = tt->row[mi];
+                lr = r.x;
+                ybase = r.y;
+                am = tt->am[j];
+            } else {
+                const int m = mi < P.c[0] ? P.a[0] + mi
+                            : (mi < P.c[1] ? P.a[1] + mi : (mi < P.c[2] ? P.a[2] + mi : P.a[3] + mi));
+                int y = P.ry + P.py * m;
+                if (y >= g.Ly) y -= g.Ly;
+                if (BLOCKED) {
+                    lr = y - g.base;
+                    if (lr < 0) lr += g.Ly;
+                } else {
+                    lr = y - g.Y0 + 2;  // y is a band row
+                }
+                ybase = y * g.Lx;
+                am = anchor_mask(x0, P, g.Lx);
+            }
             if (ls != 0) {
                 const int part = tl & ((1 << ls) - 1), bits = 32 >> ls;
                 am &= (0xFFFFFFFFu >> (32 - bits)) << (part * bits);
@@ -209,9 +257,9 @@ __device__ __forceinline__ void run_phase(const uint32_t *lat, const Geo &g, con
         uint32_t acc = unl & ~dmask;
 
         if (dq != nullptr)
-            acc |= draw_accepts_queue(dmask, S, (uint32_t)(y * g.Lx + x0), dk, thr, dq, wacc);
+            acc |= draw_accepts_queue(dmask, S, (uint32_t)(ybase + x0), dk, thr, dq, wacc);
         else
-            acc |= draw_accepts(dmask, S, (uint32_t)(y * g.Lx + x0), dk, thr);
+            acc |= draw_accepts(dmask, S, (uint32_t)(ybase + x0), dk, thr);
         const bool own = !BLOCKED || (unsigned)(lr - g.D) < (unsigned)H;
         if (own) {
             A.att += __popc(am);
@@ -266,11 +314,11 @@ template <int G, int THREADS, bool BLOCKED>
 __device__ __forceinline__ void run_phase_oi(const uint32_t *lat, const Geo &g, const PhaseR &P,
                                              const uint64_t *thr, int f, uint32_t s_lo,
                                              uint32_t s_hi, Acc &A, uint2 *dq = nullptr,
-                                             uint32_t *wacc = nullptr)
+                                             uint32_t *wacc = nullptr, const TaskTab *tt = nullptr)
 {
-    if (P.oi == 0) run_phase<G, 0, THREADS, BLOCKED>(lat, g, P, thr, f, s_lo, s_hi, A, dq, wacc);
-    else if (G == kTRI6 && P.oi == 2) run_phase<G, 2, THREADS, BLOCKED>(lat, g, P, thr, f, s_lo, s_hi, A, dq, wacc);
-    else run_phase<G, 1, THREADS, BLOCKED>(lat, g, P, thr, f, s_lo, s_hi, A, dq, wacc);
+    if (P.oi == 0) run_phase<G, 0, THREADS, BLOCKED>(lat, g, P, thr, f, s_lo, s_hi, A, dq, wacc, tt);
+    else if (G == kTRI6 && P.oi == 2) run_phase<G, 2, THREADS, BLOCKED>(lat, g, P, thr, f, s_lo, s_hi, A, dq, wacc, tt);
+    else run_phase<G, 1, THREADS, BLOCKED>(lat, g, P, thr, f, s_lo, s_hi, A, dq, wacc, tt);
 }
 
 template <typename T>
@@ -369,6 +417,7 @@ resident_sweep_kernel(const SweepJob *__restrict__ jobs, const SweepCall *__rest
     __shared__ PhaseR pp[2][8];
     __shared__ uint64_t thr[16];
     __shared__ long long red[5][kWarps];
+    __shared__ TaskTab tabs[2];  // tables of the current and the next phase
 
     const int C = (int)cluster_nctarank();
     const int rank = (int)cluster_ctarank();
@@ -413,7 +462,13 @@ resident_sweep_kernel(const SweepJob *__restrict__ jobs, const SweepCall *__rest
         lat[idx] = padded_word(J.lat, J.packing, J.pitch, y, w, g.Lx, g.W);
     }
     if (tid < 16) thr[tid] = J.thr[tid];
-    if (tid < 8) phase_table(J, g, K, Cl.sweep0, tid, &pp[0][tid]);
+    const bool table_warp = (tid >> 5) == kWarps - 1;  // builds the phase tables
+    if (table_warp) {
+        if ((tid & 31) < 8) phase_table(J, g, K, Cl.sweep0, tid & 31, &pp[0][tid & 31]);
+        __syncwarp();
+        if (blocked) build_task_table<true>(pp[0][0], g, &tabs[0]);
+        else build_task_table<false>(pp[0][0], g, &tabs[0]);
+    }
     // Every CTA of the cluster must be running before any peer writes into it.
     if (C > 1) {
         asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory");
@@ -434,19 +489,34 @@ resident_sweep_kernel(const SweepJob *__restrict__ jobs, const SweepCall *__rest
         const int buf = (int)(it & 1);
         Acc A = {0u, 0u, 0u, 0u, 0};
         for (int f = 0; f < 8; ++f) {
-            if (f == 7 && tid < 8 && it + 1 < Cl.n_mcs) phase_table(J, g, K, s + 1, tid, &pp[buf ^ 1][tid]);
+            const bool last = f == 7 && it + 1 == Cl.n_mcs;
+            if (table_warp && !last) {
+                // the next phase's tables (phase 0 of the next sweep after phase 7)
+                if (f == 7) {
+                    if ((tid & 31) < 8) phase_table(J, g, K, s + 1, tid & 31, &pp[buf ^ 1][tid & 31]);
+                    __syncwarp();
+                }
+                const PhaseR &Pn = f == 7 ? pp[buf ^ 1][0] : pp[buf][f + 1];
+                if (blocked) build_task_table<true>(Pn, g, &tabs[(f + 1) & 1]);
+                else build_task_table<false>(Pn, g, &tabs[(f + 1) & 1]);
+            }
             const PhaseR P = pp[buf][f];
+            const TaskTab *tt = &tabs[f & 1];
             if (blocked) {
-                if (J.geometry == kTRI6) run_phase_oi<kTRI6, THREADS, true>(lat, g, P, thr, f, s_lo, s_hi, A);
-                else run_phase_oi<kSQ4, THREADS, true>(lat, g, P, thr, f, s_lo, s_hi, A);
+                if (J.geometry == kTRI6)
+                    run_phase_oi<kTRI6, THREADS, true>(lat, g, P, thr, f, s_lo, s_hi, A, nullptr, nullptr, tt);
+                else
+                    run_phase_oi<kSQ4, THREADS, true>(lat, g, P, thr, f, s_lo, s_hi, A, nullptr, nullptr, tt);
                 __syncthreads();
                 if (f % K == K - 1 && !(f == 7 && it + 1 == Cl.n_mcs)) {
                     exchange_halos<THREADS>(lat, g, hmax, block & 1);
                     ++block;
                 }
             } else {
-                if (J.geometry == kTRI6) run_phase_oi<kTRI6, THREADS, false>(lat, g, P, thr, f, s_lo, s_hi, A);
-                else run_phase_oi<kSQ4, THREADS, false>(lat, g, P, thr, f, s_lo, s_hi, A);
+                if (J.geometry == kTRI6)
+                    run_phase_oi<kTRI6, THREADS, false>(lat, g, P, thr, f, s_lo, s_hi, A, nullptr, nullptr, tt);
+                else
+                    run_phase_oi<kSQ4, THREADS, false>(lat, g, P, thr, f, s_lo, s_hi, A, nullptr, nullptr, tt);
                 phase_barrier(C);
             }
         }
