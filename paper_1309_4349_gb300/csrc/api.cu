@@ -301,7 +301,7 @@ klmc_status ensure_tiled(klmc_ctx *c)
     KLMC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     c->sm_count = sms;
     if (c->helical) {
-        c->tiled = TiledPlan{1, 1, 256, 0};
+        c->tiled = TiledPlan{1, 1, 256, 0, 0};
         return KLMC_OK;
     }
     KLMC_CUDA(configure_tiled());

@@ -81,6 +81,7 @@ cudaError_t launch_resident_sweep_one(const SweepJob &job, const SweepCall &call
 //  K = 1: one launch per phase over the store in place, flips by atomics.
 struct TiledPlan {
     int H, K, threads;
+    int tables;  // 1: the band kernel keeps its K phases' task tables in shared memory
     size_t smem;
 };
 TiledPlan tiled_plan(int Lx, int Ly, int sm_count);

@@ -155,30 +155,36 @@ __device__ __forceinline__ void phase_barrier(int C)
     }
 }
 
-// Per-phase task table of a small band (at most kTabW words per row and kTabRows
-// anchor rows in the phase): the anchor mask of every word and, per task row mi,
-// the local row and the row's first site index.  The CTA's last warp builds the
-// next phase's table while the other warps run the current phase.
+// Per-phase task table: the anchor mask of every word and, per task row mi, the
+// local row and the row's first site index, so that a task loads two entries
+// instead of recomputing them.  The resident kernel keeps two (current and next
+// phase) for bands of at most kTabW words per row and kTabRows anchor rows, built by
+// the CTA's last warp while the other warps run the current phase; the band kernel
+// builds one per phase of its block at launch.
 constexpr int kTabW = 64;
-constexpr int kTabRows = 64;
+constexpr int kTabRows = 128;
 
-struct TaskTab {
-    uint32_t am[kTabW];
-    int2 row[kTabRows];  // (local row, y * Lx)
+struct TaskTab {  // a table's storage and capacity
+    uint32_t *am;
+    int2 *row;   // (local row, y * Lx)
+    int maxw, maxrows;
 };
 
-__device__ __forceinline__ bool table_fits(const Geo &g, const PhaseR &P)
+__device__ __forceinline__ bool table_fits(const Geo &g, const PhaseR &P, const TaskTab &T)
 {
-    return g.W <= kTabW && P.c[3] <= kTabRows;
+    return g.W <= T.maxw && P.c[3] <= T.maxrows;
 }
 
+// Fills the table entries with index = lane0 mod step (all of them for lane0 = 0,
+// step = 1 per thread ... ), so that a warp (step 32) or a CTA (step THREADS)
+// builds it together.
 template <bool BLOCKED>
-__device__ __forceinline__ void build_task_table(const PhaseR &P, const Geo &g, TaskTab *T)
+__device__ __forceinline__ void build_task_table(const PhaseR &P, const Geo &g, const TaskTab &T, int lane0,
+                                                 int step)
 {
-    if (!table_fits(g, P)) return;
-    const int lane = threadIdx.x & 31;
-    for (int j = lane; j < g.W; j += 32) T->am[j] = anchor_mask(j << 5, P, g.Lx);
-    for (int mi = lane; mi < P.c[3]; mi += 32) {
+    if (!table_fits(g, P, T)) return;
+    for (int j = lane0; j < g.W; j += step) T.am[j] = anchor_mask(j << 5, P, g.Lx);
+    for (int mi = lane0; mi < P.c[3]; mi += step) {
         const int m = mi < P.c[0] ? P.a[0] + mi
                     : (mi < P.c[1] ? P.a[1] + mi : (mi < P.c[2] ? P.a[2] + mi : P.a[3] + mi));
         int y = P.ry + P.py * m;
@@ -190,7 +196,7 @@ __device__ __forceinline__ void build_task_table(const PhaseR &P, const Geo &g, 
         } else {
             lr = y - g.Y0 + 2;
         }
-        T->row[mi] = make_int2(lr, y * g.Lx);
+        T.row[mi] = make_int2(lr, y * g.Lx);
     }
 }
 
@@ -215,7 +221,7 @@ __device__ __forceinline__ void run_phase(const uint32_t *lat, const Geo &g, con
     // (At 512 threads the extra evaluations cost more issue slots than they save.)
     const int ls = THREADS > 256 ? 0 : (4 * P.ntask <= THREADS ? 2 : (2 * P.ntask <= THREADS ? 1 : 0));
     const int nlane = P.ntask << ls;
-    const bool use_tab = tt != nullptr && table_fits(g, P);
+    const bool use_tab = tt != nullptr && table_fits(g, P, *tt);
     const DrawKey dk = draw_key((uint32_t)f, s_lo, s_hi, g.k0, g.k1);
     for (int t0 = threadIdx.x & ~31; t0 < nlane; t0 += THREADS) {
         const int tl = t0 + lane;
@@ -417,7 +423,8 @@ resident_sweep_kernel(const SweepJob *__restrict__ jobs, const SweepCall *__rest
     __shared__ PhaseR pp[2][8];
     __shared__ uint64_t thr[16];
     __shared__ long long red[5][kWarps];
-    __shared__ TaskTab tabs[2];  // tables of the current and the next phase
+    __shared__ uint32_t tab_am[2][kTabW];   // tables of the current and the next phase
+    __shared__ int2 tab_row[2][kTabRows];
 
     const int C = (int)cluster_nctarank();
     const int rank = (int)cluster_ctarank();
@@ -466,8 +473,9 @@ resident_sweep_kernel(const SweepJob *__restrict__ jobs, const SweepCall *__rest
     if (table_warp) {
         if ((tid & 31) < 8) phase_table(J, g, K, Cl.sweep0, tid & 31, &pp[0][tid & 31]);
         __syncwarp();
-        if (blocked) build_task_table<true>(pp[0][0], g, &tabs[0]);
-        else build_task_table<false>(pp[0][0], g, &tabs[0]);
+        const TaskTab T0 = {tab_am[0], tab_row[0], kTabW, kTabRows};
+        if (blocked) build_task_table<true>(pp[0][0], g, T0, tid & 31, 32);
+        else build_task_table<false>(pp[0][0], g, T0, tid & 31, 32);
     }
     // Every CTA of the cluster must be running before any peer writes into it.
     if (C > 1) {
@@ -497,11 +505,13 @@ resident_sweep_kernel(const SweepJob *__restrict__ jobs, const SweepCall *__rest
                     __syncwarp();
                 }
                 const PhaseR &Pn = f == 7 ? pp[buf ^ 1][0] : pp[buf][f + 1];
-                if (blocked) build_task_table<true>(Pn, g, &tabs[(f + 1) & 1]);
-                else build_task_table<false>(Pn, g, &tabs[(f + 1) & 1]);
+                const TaskTab Tn = {tab_am[(f + 1) & 1], tab_row[(f + 1) & 1], kTabW, kTabRows};
+                if (blocked) build_task_table<true>(Pn, g, Tn, tid & 31, 32);
+                else build_task_table<false>(Pn, g, Tn, tid & 31, 32);
             }
             const PhaseR P = pp[buf][f];
-            const TaskTab *tt = &tabs[f & 1];
+            const TaskTab Tc = {tab_am[f & 1], tab_row[f & 1], kTabW, kTabRows};
+            const TaskTab *tt = &Tc;
             if (blocked) {
                 if (J.geometry == kTRI6)
                     run_phase_oi<kTRI6, THREADS, true>(lat, g, P, thr, f, s_lo, s_hi, A, nullptr, nullptr, tt);
@@ -567,6 +577,24 @@ resident_sweep_kernel(const SweepJob *__restrict__ jobs, const SweepCall *__rest
     }
 }
 
+#ifndef KLMC_BAND_THREADS
+#define KLMC_BAND_THREADS 1024
+#endif
+constexpr int kBandThreads = KLMC_BAND_THREADS;  // one CTA per SM
+
+// Band kernel shared memory (32-bit words): rows (H + 2D) x RW, the warps' draw
+// queues, then (where they fit) K task tables of W words (rounded up to even) and
+// 2 x rows words each.
+__host__ __device__ __forceinline__ int band_table_rows(int H, int K)
+{
+    return (H + 4 * K) / 2 + 2;  // anchor rows of a phase over H + 2(2K - 1) rows, py >= 2
+}
+
+__host__ __device__ __forceinline__ long long band_table_offset(int H, int K, int RW)
+{
+    return (((long long)(H + 2 * (2 * K + 1)) * RW + 1) & ~1ll) + (long long)kBandThreads / 32 * kDrawQueue * 2;
+}
+
 // Tiled path, blocked: bands of H rows of a lattice too large for a cluster's
 // shared memory, one CTA each, K phases per launch.  A CTA loads its band and
 // D = 2K + 1 halo rows per side from the store `src` as it was at the launch's
@@ -577,7 +605,7 @@ resident_sweep_kernel(const SweepJob *__restrict__ jobs, const SweepCall *__rest
 template <int THREADS>
 __global__ void __launch_bounds__(THREADS, 1)
 band_phases_kernel(const SweepJob J, const void *__restrict__ src, void *__restrict__ dst, int H, int K,
-                   int k, int f0)
+                   int tables, int k, int f0)
 {
     constexpr int kWarps = THREADS / 32;
     extern __shared__ __align__(16) uint32_t lat[];
@@ -617,6 +645,18 @@ band_phases_kernel(const SweepJob J, const void *__restrict__ src, void *__restr
     if (tid < 16) thr[tid] = J.thr[tid];
     if (tid < K) phase_table(J, g, K, s, f0 + tid, &pp[tid]);
     __syncthreads();
+    // The block's task tables follow the rows and the draw queues.
+    const int tab_rows = band_table_rows(H, K);
+    const int tab_w = (g.W + 1) & ~1;  // even, so that the int2 row entries stay aligned
+    uint32_t *const tab_base = lat + band_table_offset(H, K, g.RW);
+    if (tables) {
+        for (int q = 0; q < K; ++q) {
+            uint32_t *const t = tab_base + (size_t)q * (tab_w + 2 * tab_rows);
+            const TaskTab T = {t, (int2 *)(t + tab_w), g.W, tab_rows};
+            build_task_table<true>(pp[q], g, T, tid, THREADS);
+        }
+        __syncthreads();
+    }
 
     Acc A = {0u, 0u, 0u, 0u, 0};
     // the warps' draw queues follow the rows (H + 2D rows of the tallest band)
@@ -625,8 +665,13 @@ band_phases_kernel(const SweepJob J, const void *__restrict__ src, void *__restr
     uint32_t *const wacc = wacc_all + (tid & ~31);
     for (int j = 0; j < K; ++j) {
         const PhaseR P = pp[j];
-        if (J.geometry == kTRI6) run_phase_oi<kTRI6, THREADS, true>(lat, g, P, thr, f0 + j, s_lo, s_hi, A, dq, wacc);
-        else run_phase_oi<kSQ4, THREADS, true>(lat, g, P, thr, f0 + j, s_lo, s_hi, A, dq, wacc);
+        uint32_t *const t = tab_base + (size_t)j * (tab_w + 2 * tab_rows);
+        const TaskTab T = {t, (int2 *)(t + tab_w), g.W, tab_rows};
+        const TaskTab *const tt = tables ? &T : nullptr;
+        if (J.geometry == kTRI6)
+            run_phase_oi<kTRI6, THREADS, true>(lat, g, P, thr, f0 + j, s_lo, s_hi, A, dq, wacc, tt);
+        else
+            run_phase_oi<kSQ4, THREADS, true>(lat, g, P, thr, f0 + j, s_lo, s_hi, A, dq, wacc, tt);
         __syncthreads();
     }
 
@@ -767,31 +812,32 @@ cudaError_t launch_resident_sweep_one(const SweepJob &job, const SweepCall &call
 #ifndef KLMC_TILED_BLOCK
 #define KLMC_TILED_BLOCK 4
 #endif
-#ifndef KLMC_BAND_THREADS
-#define KLMC_BAND_THREADS 1024
-#endif
-constexpr int kBandThreads = KLMC_BAND_THREADS;  // one CTA per SM
+
 
 TiledPlan tiled_band_plan(int Lx, int Ly, int sm_count)
 {
     TiledPlan p;
-    const long long RW = (Lx + 95) / 32;
-    const long long queue_bytes = (long long)kBandThreads / 32 * kDrawQueue * 8 + 8;
-    const long long max_rows = (kResidentMaxSmem - queue_bytes) / (RW * 4);
+    const long long RW = (Lx + 95) / 32, W = (((Lx + 31) / 32) + 1) & ~1ll;
     for (int K = KLMC_TILED_BLOCK; K >= 2; K >>= 1) {
         const int D = 2 * K + 1;
         long long H = (Ly + sm_count - 1) / sm_count;  // one CTA per SM
-        if (H + 2 * D > max_rows) H = max_rows - 2 * D;  // more bands than SMs
-        if (H < 1 || H + 2 * D > Ly) continue;         // a band's rows must not wrap onto themselves
+        // rows and draw queues must fit: shrink the bands (more bands than SMs)
+        // until they do
+        while (H >= 1 && 4 * band_table_offset((int)H, K, (int)RW) > kResidentMaxSmem) --H;
+        if (H < 1 || H + 2 * D > Ly) continue;  // a band's rows must not wrap onto themselves
+        const long long rows = 4 * band_table_offset((int)H, K, (int)RW);
+        const long long tabs = 4 * K * (W + 2 * band_table_rows((int)H, K));
         p.H = (int)H;
         p.K = K;
         p.threads = kBandThreads;
-        p.smem = (size_t)((((H + 2 * D) * RW + 1) & ~1ll) * 4 + (long long)kBandThreads / 32 * kDrawQueue * 8);
+        p.tables = rows + tabs <= kResidentMaxSmem ? 1 : 0;  // the task tables where they fit
+        p.smem = (size_t)(rows + (p.tables ? tabs : 0));
         return p;
     }
     p.H = 0;
     p.K = 1;
     p.threads = 0;
+    p.tables = 0;
     p.smem = 0;
     return p;
 }
@@ -813,8 +859,8 @@ cudaError_t launch_band_phases(const SweepJob &job, const TiledPlan &plan, const
                                int k, int f0, cudaStream_t stream)
 {
     const int grid = (job.Ly + plan.H - 1) / plan.H;
-    band_phases_kernel<kBandThreads><<<grid, kBandThreads, plan.smem, stream>>>(job, src, dst, plan.H, plan.K, k,
-                                                                               f0);
+    band_phases_kernel<kBandThreads><<<grid, kBandThreads, plan.smem, stream>>>(job, src, dst, plan.H, plan.K,
+                                                                               plan.tables, k, f0);
     return cudaGetLastError();
 }
 
