@@ -64,9 +64,9 @@ INT32_LANES_PER_SM = 64
 # of the 400x400 x 5 workload; profiles/band_phases_8192x8192_ncu.md: one 4-phase band
 # launch of the 8192x8192 lattice), valid only for the kernel sources they were taken
 # with (hash of sweep_resident.cu + sweep_common.cuh).
-TRAFFIC_C2_LAUNCH = 222208
-TRAFFIC_C3_LAUNCH = 8469504
-TRAFFIC_SOURCES = "f6f30b7940720d70"
+TRAFFIC_C2_LAUNCH = 222464
+TRAFFIC_C3_LAUNCH = 8473344
+TRAFFIC_SOURCES = "8018ea97bd08f949"
 
 
 
