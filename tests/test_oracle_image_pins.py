@@ -12,6 +12,7 @@ import numpy as np
 import pytest
 
 import oracle
+from _golden import paper_value
 
 MOORE = [(1, 0), (1, 1), (0, 1), (-1, 1), (-1, 0), (-1, -1), (0, -1), (1, -1)]
 
@@ -130,5 +131,6 @@ def test_papers_image_ffn_agreement_at_natural_resolution():
     U = oracle.natural_width(Lx, Ly)
     H = int(round(U * Ly * (3 ** 0.5 / 2) / (U / 2)))
     image, mask = oracle.snapshot(Lx, Ly, r.lattice, U, H, 1)
-    img = np.mean([s / p for s, p in (oracle.image_ffn(image, mask, 35, 3, m) for m in range(8))])
-    assert abs(img - raw) < 1e-3
+    delta = paper_value("delta_col")
+    img = np.mean([s / p for s, p in (oracle.image_ffn(image, mask, delta, 3, m) for m in range(8))])
+    assert abs(img - raw) < paper_value("image_ffn_max_diff")
