@@ -121,9 +121,12 @@ klmc_status klmc_create_ex(klmc_ctx **out, const klmc_params *p);
  * phases of exchange attempts, N attempts when 4 | Lx and 4 | Ly (section
  * "Massive Parallel Kawasaki Kinetics": one MPKK step = as many attempts as
  * sites).  Deterministic: the result depends only on seed, the lattice and the
- * absolute sweep index, not on the cluster size.  EINVAL when the lattice is
- * too large for the shared-memory resident path (each CTA's band of padded bit
- * rows plus four halo rows must fit its shared memory). */
+ * absolute sweep index, not on the cluster size.  With the automatic launch shape
+ * (cluster = 0) a lattice too large for one thread-block cluster's shared memory
+ * runs on the tiled path: bands of rows, one CTA each, four phases per launch,
+ * rows of a bit store on 16-byte boundaries moved by bulk copies.  With an explicit
+ * cluster size, EINVAL when the lattice does not fit it (each CTA's band of padded
+ * bit rows plus its halo rows must fit its shared memory). */
 klmc_status klmc_sweep(klmc_ctx *c, int64_t n_mcs);
 
 /* As klmc_sweep, and records n_unlike after every trace_every-th step into the
@@ -133,7 +136,9 @@ klmc_status klmc_sweep_traced(klmc_ctx *c, int64_t n_mcs, int64_t trace_every,
 
 /* Number of unlike contacts (kept exactly, updated by every accepted exchange)
  * and E/kT = omega/kT * n_unlike (energy model of the omega_AB equation).
- * Synchronises.  Either pointer may be NULL. */
+ * Synchronises.  Either pointer may be NULL.  KLMC_ETIMEOUT if a tiled launch
+ * of this handle gave up its bounded wait for its row copies: that launch left
+ * its band unwritten, so the lattice is no longer a state of the chain. */
 klmc_status klmc_energy(klmc_ctx *c, int64_t *n_unlike, double *energy_over_kT);
 
 /* Recounts n_unlike from the lattice on the device (every bond once) without
@@ -219,7 +224,7 @@ klmc_status klmc_cluster_histogram_noalloc(const void *dev_lattice, int32_t pack
                                            int64_t *dev_counts, int64_t capacity,
                                            int64_t *dev_n_distinct, void *stream);
 
-/* Counters (see klmc_counters).  Synchronises. */
+/* Counters (see klmc_counters).  Synchronises.  KLMC_ETIMEOUT as klmc_energy. */
 klmc_status klmc_get_counters(klmc_ctx *c, klmc_counters *out);
 
 /* Copies the lattice to host memory, one byte per site (n must equal Lx*Ly).

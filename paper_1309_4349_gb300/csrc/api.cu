@@ -265,6 +265,9 @@ klmc_status create_one(klmc_ctx **out, const klmc_params *p, klmc_batch *owner, 
         return st;
     }
     cudaError_t e = cudaMemsetAsync(c->state, 0, kStateSlots * sizeof(long long), c->stream);
+    // The store's row padding (words or bytes past the last site) stays zero: every
+    // writer writes sites only, or whole rows with zero padding.
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->lat, 0, c->lat_bytes, c->stream);
     if (e == cudaSuccess)
         e = launch_init_lattice(c->lat, J.packing, p->Lx, p->Ly, c->pitch, J.key0, J.key1, c->nA,
                                 c->init_scratch, c->stream);
@@ -309,6 +312,7 @@ klmc_status ensure_tiled(klmc_ctx *c)
     if (plan.K >= 2) {
         c->tiled_alt = dev_alloc(c, c->lat_bytes);
         if (!c->tiled_alt) return fail(KLMC_ENOMEM, "device allocation of the tiled path's second buffer failed");
+        KLMC_CUDA(cudaMemsetAsync(c->tiled_alt, 0, c->lat_bytes, c->stream));
     }
     c->tiled = plan;
     return KLMC_OK;
@@ -643,11 +647,12 @@ klmc_status klmc_sweep_traced(klmc_ctx *c, int64_t n_mcs, int64_t trace_every, i
 klmc_status klmc_energy(klmc_ctx *c, int64_t *n_unlike, double *energy_over_kT)
 {
     if (!c) return fail(KLMC_EINVAL, "ctx is NULL");
-    long long v = 0;
-    KLMC_CUDA(cudaMemcpyAsync(&v, c->state + kNUnlike, sizeof(v), cudaMemcpyDeviceToHost, c->stream));
+    long long v[kStateSlots];
+    KLMC_CUDA(cudaMemcpyAsync(v, c->state, sizeof(v), cudaMemcpyDeviceToHost, c->stream));
     KLMC_CUDA(cudaStreamSynchronize(c->stream));
-    if (n_unlike) *n_unlike = v;
-    if (energy_over_kT) *energy_over_kT = c->p.omega_over_kT * (double)v;
+    if (v[kFault]) return fail(KLMC_ETIMEOUT, "a tiled sweep launch gave up waiting for its row copies");
+    if (n_unlike) *n_unlike = v[kNUnlike];
+    if (energy_over_kT) *energy_over_kT = c->p.omega_over_kT * (double)v[kNUnlike];
     return KLMC_OK;
 }
 
@@ -776,6 +781,7 @@ klmc_status klmc_get_counters(klmc_ctx *c, klmc_counters *out)
     long long v[kStateSlots];
     KLMC_CUDA(cudaMemcpyAsync(v, c->state, sizeof(v), cudaMemcpyDeviceToHost, c->stream));
     KLMC_CUDA(cudaStreamSynchronize(c->stream));
+    if (v[kFault]) return fail(KLMC_ETIMEOUT, "a tiled sweep launch gave up waiting for its row copies");
     out->sweeps = c->sweep;
     out->attempts = v[kAttempts];
     out->unlike = v[kUnlike];

@@ -25,7 +25,8 @@ enum StateSlot : int {
     kTracePos = 8,  // next entry of the energy trace (tiled path)
     kTracePtr = 9,  // device address of the energy trace (tiled path)
     kFfn = 10,      // random-neighbour count of klmc_ffn; with slot 11, klmc_image_ffn's counts
-    kStateSlots = 12
+    kFault = 12,    // nonzero: a tiled launch gave up waiting for its row copies (band left unwritten)
+    kStateSlots = 13
 };
 
 // Static description of one lattice for the sweep kernels.

@@ -582,18 +582,44 @@ resident_sweep_kernel(const SweepJob *__restrict__ jobs, const SweepCall *__rest
 #endif
 constexpr int kBandThreads = KLMC_BAND_THREADS;  // one CTA per SM
 
-// Band kernel shared memory (32-bit words): rows (H + 2D) x RW, the warps' draw
+// Band kernel shared memory (32-bit words): rows (H + 2D) x RWb, the warps' draw
 // queues, then (where they fit) K task tables of W words (rounded up to even) and
-// 2 x rows words each.
+// 2 x rows words each.  A band row is the padded row of the resident kernel (word 0
+// holds position -1, words 1..W the sites, W+1 the last pads) placed 3 words into
+// RWb = W + 5 rounded up to 4 words, so that its sites start on a 16-byte boundary
+// and a row of the bit store lands there by one bulk copy.
+__host__ __device__ __forceinline__ int band_row_words(int W)
+{
+    return (W + 5 + 3) / 4 * 4;
+}
+
 __host__ __device__ __forceinline__ int band_table_rows(int H, int K)
 {
     return (H + 4 * K) / 2 + 2;  // anchor rows of a phase over H + 2(2K - 1) rows, py >= 2
 }
 
-__host__ __device__ __forceinline__ long long band_table_offset(int H, int K, int RW)
+__host__ __device__ __forceinline__ long long band_table_offset(int H, int K, int RWb)
 {
-    return (((long long)(H + 2 * (2 * K + 1)) * RW + 1) & ~1ll) + (long long)kBandThreads / 32 * kDrawQueue * 2;
+    return (long long)(H + 2 * (2 * K + 1)) * RWb + (long long)kBandThreads / 32 * kDrawQueue * 2;
 }
+
+// Waits for phase `parity` of the mbarrier at shared address mbar, giving up after
+// `limit` polls.
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, int limit)
+{
+    for (int i = 0; i < limit; ++i) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done) : "r"(mbar), "r"(parity) : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+constexpr int kCopyWaitPolls = 1 << 20;
 
 // Tiled path, blocked: bands of H rows of a lattice too large for a cluster's
 // shared memory, one CTA each, K phases per launch.  A CTA loads its band and
@@ -602,21 +628,24 @@ __host__ __device__ __forceinline__ long long band_table_offset(int H, int K, in
 // only the band's anchors counted), and writes its band to `dst`.  Reading one
 // buffer and writing the other keeps every CTA's halo at the launch's starting
 // state while other CTAs finish; the launch boundary orders the blocks.
+// Bit stores on 16-byte boundaries move their rows by bulk copies (the TMA unit:
+// one copy per row in, one per band row out); other stores word by word.
 template <int THREADS>
 __global__ void __launch_bounds__(THREADS, 1)
 band_phases_kernel(const SweepJob J, const void *__restrict__ src, void *__restrict__ dst, int H, int K,
                    int tables, int k, int f0)
 {
     constexpr int kWarps = THREADS / 32;
-    extern __shared__ __align__(16) uint32_t lat[];
+    extern __shared__ __align__(16) uint32_t smem[];
     __shared__ PhaseR pp[8];
     __shared__ uint64_t thr[16];
     __shared__ long long red[5][kWarps];
     __shared__ uint32_t wacc_all[THREADS];  // per-warp accept words of queued draws
+    __shared__ __align__(8) unsigned long long copy_bar;
     wacc_all[threadIdx.x] = 0u;
 
     Geo g;
-    g.Lx = J.Lx; g.Ly = J.Ly; g.W = J.W; g.RW = J.RW; g.magicW = J.magicW;
+    g.Lx = J.Lx; g.Ly = J.Ly; g.W = J.W; g.RW = band_row_words(J.W); g.magicW = J.magicW;
     g.k0 = J.key0; g.k1 = J.key1;
     g.zm1 = (J.geometry == kTRI6 ? 6 : 4) - 1;
     g.sign = J.draw_lo > J.draw_hi ? 0 : (J.draw_lo == 0 ? -1 : 1);
@@ -625,22 +654,78 @@ band_phases_kernel(const SweepJob J, const void *__restrict__ src, void *__restr
     g.Y0 = (int)blockIdx.x * H;
     g.Y1 = min(g.Y0 + H, g.Ly);
     g.prevY = g.prevH = g.nextY = g.nextH = 0;
+    uint32_t *const lat = smem + 3;  // padded row lr, word w: lat[lr * RWb + w]
     g.lat_addr = smem_addr(lat);
     g.D = 2 * K + 1;
     g.base = g.Y0 - g.D < 0 ? g.Y0 - g.D + g.Ly : g.Y0 - g.D;
     const int tid = threadIdx.x;
     const int Hc = g.Y1 - g.Y0;
     const int NL = Hc + 2 * g.D;
+    const int RWb = g.RW;
     const long long s = J.state[kSweepBase] + k;
     const uint32_t s_lo = (uint32_t)(unsigned long long)s;
     const uint32_t s_hi = (uint32_t)((unsigned long long)s >> 32);
+    const bool bulk = J.packing == kPackBit && ((((uintptr_t)src) | ((uintptr_t)dst)) & 15u) == 0u &&
+                      (J.pitch & 3) == 0 && J.pitch + 4 <= RWb;
+    const uint32_t row_bytes = 4u * (uint32_t)J.pitch;
 
-    for (int idx = tid; idx < NL * g.RW; idx += THREADS) {
-        const int lr = idx / g.RW, w = idx - lr * g.RW;
-        int y = g.Y0 - g.D + lr;
-        if (y < 0) y += g.Ly;
-        if (y >= g.Ly) y -= g.Ly;
-        lat[idx] = padded_word(src, J.packing, J.pitch, y, w, g.Lx, g.W);
+    if (bulk) {
+        // One bulk copy per row (pitch words, 16-byte aligned at both ends) into the
+        // row's site words, completing on one mbarrier; then the pad words.
+        const uint32_t bar = smem_addr(&copy_bar);
+        if (tid == 0) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        }
+        __syncthreads();
+        if (tid < 32) {
+            if (tid == 0) {
+                unsigned long long st;
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 %0, [%1], %2;"
+                             : "=l"(st) : "r"(bar), "r"(row_bytes * (uint32_t)NL) : "memory");
+            }
+            __syncwarp();
+            for (int lr = tid; lr < NL; lr += 32) {
+                int y = g.Y0 - g.D + lr;
+                if (y < 0) y += g.Ly;
+                if (y >= g.Ly) y -= g.Ly;
+                const char *from = (const char *)src + (size_t)y * row_bytes;
+                const uint32_t to = smem_addr(lat + (size_t)lr * RWb + 1);
+                asm volatile(
+                    "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                    ::"r"(to), "l"(from), "r"(row_bytes), "r"(bar) : "memory");
+            }
+        }
+        const bool ok = mbar_wait(bar, 0u, kCopyWaitPolls);
+        if (__syncthreads_or(!ok)) {
+            // Give up on this launch: report it, let the copies in flight land, and
+            // leave the band unwritten.
+            if (tid == 0) atomicExch((unsigned long long *)&J.state[kFault], 1ull);
+            mbar_wait(bar, 0u, kCopyWaitPolls);
+            return;
+        }
+        for (int lr = tid; lr < NL; lr += THREADS) {
+            uint32_t *row = lat + (size_t)lr * RWb;
+            const int xl = g.Lx - 1;
+            const uint32_t s01 = row[1] & 3u;
+            const uint32_t last = (row[(xl >> 5) + 1] >> (xl & 31)) & 1u;
+            const int nvalid = g.Lx - 32 * (g.W - 1);
+            if (nvalid < 32) row[g.W] &= (1u << nvalid) - 1u;
+            for (int w = g.W + 1; w <= J.pitch; ++w) row[w] = 0u;  // beyond the sites
+            row[g.W + 1] = 0u;
+            row[(g.Lx + 32) >> 5] |= (s01 & 1u) << (g.Lx & 31);       // position Lx: site 0
+            row[(g.Lx + 33) >> 5] |= (s01 >> 1) << ((g.Lx + 1) & 31);  // position Lx + 1: site 1
+            row[0] = last << 31;                                         // position -1: site Lx - 1
+        }
+    } else {
+        for (int idx = tid; idx < NL * (g.W + 2); idx += THREADS) {
+            const int lr = idx / (g.W + 2), w = idx - lr * (g.W + 2);
+            int y = g.Y0 - g.D + lr;
+            if (y < 0) y += g.Ly;
+            if (y >= g.Ly) y -= g.Ly;
+            lat[(size_t)lr * RWb + w] = padded_word(src, J.packing, J.pitch, y, w, g.Lx, g.W);
+        }
     }
     if (tid < 16) thr[tid] = J.thr[tid];
     if (tid < K) phase_table(J, g, K, s, f0 + tid, &pp[tid]);
@@ -648,7 +733,7 @@ band_phases_kernel(const SweepJob J, const void *__restrict__ src, void *__restr
     // The block's task tables follow the rows and the draw queues.
     const int tab_rows = band_table_rows(H, K);
     const int tab_w = (g.W + 1) & ~1;  // even, so that the int2 row entries stay aligned
-    uint32_t *const tab_base = lat + band_table_offset(H, K, g.RW);
+    uint32_t *const tab_base = smem + band_table_offset(H, K, RWb);
     if (tables) {
         for (int q = 0; q < K; ++q) {
             uint32_t *const t = tab_base + (size_t)q * (tab_w + 2 * tab_rows);
@@ -660,8 +745,7 @@ band_phases_kernel(const SweepJob J, const void *__restrict__ src, void *__restr
 
     Acc A = {0u, 0u, 0u, 0u, 0};
     // the warps' draw queues follow the rows (H + 2D rows of the tallest band)
-    uint2 *const dq = (uint2 *)(lat + (((size_t)(H + 2 * g.D) * g.RW + 1) & ~(size_t)1)) +
-                      (size_t)(tid >> 5) * kDrawQueue;
+    uint2 *const dq = (uint2 *)(smem + (size_t)(H + 2 * g.D) * RWb) + (size_t)(tid >> 5) * kDrawQueue;
     uint32_t *const wacc = wacc_all + (tid & ~31);
     for (int j = 0; j < K; ++j) {
         const PhaseR P = pp[j];
@@ -675,18 +759,40 @@ band_phases_kernel(const SweepJob J, const void *__restrict__ src, void *__restr
         __syncthreads();
     }
 
-    for (int idx = tid; idx < Hc * g.W; idx += THREADS) {
-        const int r = idx / g.W, w = idx - r * g.W;
-        const int y = g.Y0 + r;
-        const uint32_t v = lat[(size_t)(r + g.D) * g.RW + w + 1];
-        const int pos0 = 32 * w;
-        const int nvalid = min(32, g.Lx - pos0);
-        if (J.packing == kPackBit) {
-            const uint32_t valid = nvalid == 32 ? 0xFFFFFFFFu : ((1u << nvalid) - 1u);
-            ((uint32_t *)dst)[(size_t)y * J.pitch + w] = v & valid;
-        } else {
-            uint8_t *row = (uint8_t *)dst + (size_t)y * J.pitch;
-            for (int b = 0; b < nvalid; ++b) row[pos0 + b] = (uint8_t)((v >> b) & 1u);
+    if (bulk) {
+        // The band's rows as stored: sites only, then one bulk copy per row.
+        for (int r = tid; r < Hc; r += THREADS) {
+            uint32_t *row = lat + (size_t)(r + g.D) * RWb;
+            const int nvalid = g.Lx - 32 * (g.W - 1);
+            if (nvalid < 32) row[g.W] &= (1u << nvalid) - 1u;
+            for (int w = g.W + 1; w <= J.pitch; ++w) row[w] = 0u;
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid < 32) {
+            for (int r = tid; r < Hc; r += 32) {
+                char *to = (char *)dst + (size_t)(g.Y0 + r) * row_bytes;
+                const uint32_t from = smem_addr(lat + (size_t)(r + g.D) * RWb + 1);
+                asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;"
+                             ::"l"(to), "r"(from), "r"(row_bytes) : "memory");
+            }
+            asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+            asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+        }
+    } else {
+        for (int idx = tid; idx < Hc * g.W; idx += THREADS) {
+            const int r = idx / g.W, w = idx - r * g.W;
+            const int y = g.Y0 + r;
+            const uint32_t v = lat[(size_t)(r + g.D) * RWb + w + 1];
+            const int pos0 = 32 * w;
+            const int nvalid = min(32, g.Lx - pos0);
+            if (J.packing == kPackBit) {
+                const uint32_t valid = nvalid == 32 ? 0xFFFFFFFFu : ((1u << nvalid) - 1u);
+                ((uint32_t *)dst)[(size_t)y * J.pitch + w] = v & valid;
+            } else {
+                uint8_t *row = (uint8_t *)dst + (size_t)y * J.pitch;
+                for (int b = 0; b < nvalid; ++b) row[pos0 + b] = (uint8_t)((v >> b) & 1u);
+            }
         }
     }
 
@@ -817,15 +923,16 @@ cudaError_t launch_resident_sweep_one(const SweepJob &job, const SweepCall &call
 TiledPlan tiled_band_plan(int Lx, int Ly, int sm_count)
 {
     TiledPlan p;
-    const long long RW = (Lx + 95) / 32, W = (((Lx + 31) / 32) + 1) & ~1ll;
+    const int RWb = band_row_words((Lx + 31) / 32);
+    const long long W = (((Lx + 31) / 32) + 1) & ~1ll;
     for (int K = KLMC_TILED_BLOCK; K >= 2; K >>= 1) {
         const int D = 2 * K + 1;
         long long H = (Ly + sm_count - 1) / sm_count;  // one CTA per SM
         // rows and draw queues must fit: shrink the bands (more bands than SMs)
         // until they do
-        while (H >= 1 && 4 * band_table_offset((int)H, K, (int)RW) > kResidentMaxSmem) --H;
+        while (H >= 1 && 4 * band_table_offset((int)H, K, RWb) > kResidentMaxSmem) --H;
         if (H < 1 || H + 2 * D > Ly) continue;  // a band's rows must not wrap onto themselves
-        const long long rows = 4 * band_table_offset((int)H, K, (int)RW);
+        const long long rows = 4 * band_table_offset((int)H, K, RWb);
         const long long tabs = 4 * K * (W + 2 * band_table_rows((int)H, K));
         p.H = (int)H;
         p.K = K;
