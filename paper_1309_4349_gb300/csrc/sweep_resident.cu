@@ -642,6 +642,8 @@ band_phases_kernel(const SweepJob J, const void *__restrict__ src, void *__restr
     __shared__ long long red[5][kWarps];
     __shared__ uint32_t wacc_all[THREADS];  // per-warp accept words of queued draws
     __shared__ __align__(8) unsigned long long copy_bar;
+    // The next launch may be scheduled now; it waits for this one before it reads.
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     wacc_all[threadIdx.x] = 0u;
 
     Geo g;
@@ -662,22 +664,26 @@ band_phases_kernel(const SweepJob J, const void *__restrict__ src, void *__restr
     const int Hc = g.Y1 - g.Y0;
     const int NL = Hc + 2 * g.D;
     const int RWb = g.RW;
-    const long long s = J.state[kSweepBase] + k;
-    const uint32_t s_lo = (uint32_t)(unsigned long long)s;
-    const uint32_t s_hi = (uint32_t)((unsigned long long)s >> 32);
     const bool bulk = J.packing == kPackBit && ((((uintptr_t)src) | ((uintptr_t)dst)) & 15u) == 0u &&
                       (J.pitch & 3) == 0 && J.pitch + 4 <= RWb;
     const uint32_t row_bytes = 4u * (uint32_t)J.pitch;
+    const uint32_t bar = smem_addr(&copy_bar);
+    if (bulk && tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    // Everything below reads what earlier launches on the stream wrote.
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    if (tid < 16) thr[tid] = J.thr[tid];
+    const long long s = J.state[kSweepBase] + k;
+    const uint32_t s_lo = (uint32_t)(unsigned long long)s;
+    const uint32_t s_hi = (uint32_t)((unsigned long long)s >> 32);
+    if (tid < K) phase_table(J, g, K, s, f0 + tid, &pp[tid]);
 
     if (bulk) {
         // One bulk copy per row (pitch words, 16-byte aligned at both ends) into the
         // row's site words, completing on one mbarrier; then the pad words.
-        const uint32_t bar = smem_addr(&copy_bar);
-        if (tid == 0) {
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
-            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        }
         __syncthreads();
         if (tid < 32) {
             if (tid == 0) {
@@ -727,8 +733,6 @@ band_phases_kernel(const SweepJob J, const void *__restrict__ src, void *__restr
             lat[(size_t)lr * RWb + w] = padded_word(src, J.packing, J.pitch, y, w, g.Lx, g.W);
         }
     }
-    if (tid < 16) thr[tid] = J.thr[tid];
-    if (tid < K) phase_table(J, g, K, s, f0 + tid, &pp[tid]);
     __syncthreads();
     // The block's task tables follow the rows and the draw queues.
     const int tab_rows = band_table_rows(H, K);
@@ -965,9 +969,21 @@ cudaError_t configure_band()
 cudaError_t launch_band_phases(const SweepJob &job, const TiledPlan &plan, const void *src, void *dst,
                                int k, int f0, cudaStream_t stream)
 {
-    const int grid = (job.Ly + plan.H - 1) / plan.H;
-    band_phases_kernel<kBandThreads><<<grid, kBandThreads, plan.smem, stream>>>(job, src, dst, plan.H, plan.K,
-                                                                               plan.tables, k, f0);
+    // Programmatic dependent launch: the CTAs of this launch may be scheduled while
+    // the previous one drains, and wait for it in the kernel before reading.
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)((job.Ly + plan.H - 1) / plan.H), 1, 1);
+    cfg.blockDim = dim3(kBandThreads, 1, 1);
+    cfg.dynamicSmemBytes = plan.smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, band_phases_kernel<kBandThreads>, job, src, dst, plan.H, plan.K,
+                                       plan.tables, k, f0);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
