@@ -381,16 +381,20 @@ __device__ __forceinline__ uint32_t draw_accepts(uint32_t dmask, const Planes &S
 }
 
 // Accept bits of this lane's dmask when the warp's draws are drawn by all its
-// lanes.  Every lane appends its draws (site index, S, bit, lane) to the warp's
-// queue q at its prefix-sum offset; then lane i draws entries i and i + 32 of
-// every 64 (two Philox chains interleaved) and returns accepted bits to their
-// lanes through wacc (the warp's 32 words of shared memory, zero on entry and on
-// return).  When the warp has more than kDrawQueue draws, each lane draws its own.
-// Every lane of the warp must call it.
+// lanes.  Every lane stores its S planes and first site index once, and appends
+// its draws (lane, bit) as 16-bit entries to the warp's queue at its prefix-sum
+// offset; then lane i draws entries i and i + 32 of every 64 (two Philox chains
+// interleaved), reading the entry's S and site from its owner's record, and
+// returns accepted bits to their lanes through wacc (the warp's 32 words of shared
+// memory, zero on entry and on return).  When the warp has more than kDrawQueue
+// draws, each lane draws its own.  Every lane of the warp must call it.
+// The warp's region q (16-byte aligned, kDrawQueueWords words): planes uint4[32],
+// sites uint32[32], entries uint16[kDrawQueue].
 constexpr int kDrawQueue = 256;
+constexpr int kDrawQueueWords = 32 * 4 + 32 + kDrawQueue / 2;
 
 __device__ __forceinline__ uint32_t draw_accepts_queue(uint32_t dmask, const Planes &S, uint32_t site_base,
-                                                       const DrawKey &dk, const uint64_t *thr, uint2 *q,
+                                                       const DrawKey &dk, const uint64_t *thr, uint32_t *q,
                                                        uint32_t *wacc)
 {
     if (!__any_sync(0xFFFFFFFFu, dmask != 0u)) return 0u;
@@ -404,25 +408,36 @@ __device__ __forceinline__ uint32_t draw_accepts_queue(uint32_t dmask, const Pla
     }
     const int total = __shfl_sync(0xFFFFFFFFu, incl, 31);
     if (total > kDrawQueue) return draw_accepts(dmask, S, site_base, dk, thr);
+    uint4 *const planes = (uint4 *)q;
+    uint32_t *const sites = (uint32_t *)(planes + 32);
+    uint16_t *const ent = (uint16_t *)(sites + 32);
+    if (nd != 0) {
+        planes[lane] = make_uint4(S.s0, S.s1, S.s2, S.s3);
+        sites[lane] = site_base;
+    }
     int slot = incl - nd;
+    const uint32_t tag = (uint32_t)lane << 5;
     uint32_t dm = dmask;
     while (dm != 0u) {
         const int p = __ffs(dm) - 1;
         dm &= dm - 1u;
-        const uint32_t Sp = ((S.s0 >> p) & 1u) | (((S.s1 >> p) & 1u) << 1) | (((S.s2 >> p) & 1u) << 2) |
-                            (((S.s3 >> p) & 1u) << 3);
-        q[slot++] = make_uint2(site_base + (uint32_t)p, Sp | ((uint32_t)p << 4) | ((uint32_t)lane << 9));
+        ent[slot++] = (uint16_t)(tag | (uint32_t)p);
     }
     __syncwarp();
     for (int k = lane; k < total; k += 64) {
-        const uint2 e1 = q[k];
+        const uint32_t e1 = ent[k];
         const bool two = k + 32 < total;
-        const uint2 e2 = two ? q[k + 32] : e1;
+        const uint32_t e2 = two ? ent[k + 32] : e1;
+        const uint32_t l1 = e1 >> 5, p1 = e1 & 31u, l2 = e2 >> 5, p2 = e2 & 31u;
         uint32_t r1, r2;
-        philox2_w0_key(e1.x, e2.x, dk, r1, r2);
-        if ((uint64_t)r1 < thr[e1.y & 15u]) atomicOr(wacc + ((e1.y >> 9) & 31u), 1u << ((e1.y >> 4) & 31u));
-        if (two && (uint64_t)r2 < thr[e2.y & 15u])
-            atomicOr(wacc + ((e2.y >> 9) & 31u), 1u << ((e2.y >> 4) & 31u));
+        philox2_w0_key(sites[l1] + p1, sites[l2] + p2, dk, r1, r2);
+        const uint4 a = planes[l1], b = planes[l2];
+        const uint32_t S1 = ((a.x >> p1) & 1u) | (((a.y >> p1) & 1u) << 1) | (((a.z >> p1) & 1u) << 2) |
+                            (((a.w >> p1) & 1u) << 3);
+        const uint32_t S2 = ((b.x >> p2) & 1u) | (((b.y >> p2) & 1u) << 1) | (((b.z >> p2) & 1u) << 2) |
+                            (((b.w >> p2) & 1u) << 3);
+        if ((uint64_t)r1 < thr[S1]) atomicOr(wacc + l1, 1u << p1);
+        if (two && (uint64_t)r2 < thr[S2]) atomicOr(wacc + l2, 1u << p2);
     }
     __syncwarp();
     const uint32_t acc = wacc[lane];

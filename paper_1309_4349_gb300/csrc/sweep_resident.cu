@@ -207,7 +207,7 @@ __device__ __forceinline__ void build_task_table(const PhaseR &P, const Geo &g, 
 template <int G, int OI, int THREADS, bool BLOCKED>
 __device__ __forceinline__ void run_phase(const uint32_t *lat, const Geo &g, const PhaseR &P,
                                           const uint64_t *thr, int f,
-                                          uint32_t s_lo, uint32_t s_hi, Acc &A, uint2 *dq = nullptr,
+                                          uint32_t s_lo, uint32_t s_hi, Acc &A, uint32_t *dq = nullptr,
                                           uint32_t *wacc = nullptr, const TaskTab *tt = nullptr)
 {
     // b = a + o: (1,0) -> same row, +1; (0,1) -> next row; (1,-1) -> previous row, +1
@@ -319,7 +319,7 @@ __device__ __forceinline__ void run_phase(const uint32_t *lat, const Geo &g, con
 template <int G, int THREADS, bool BLOCKED>
 __device__ __forceinline__ void run_phase_oi(const uint32_t *lat, const Geo &g, const PhaseR &P,
                                              const uint64_t *thr, int f, uint32_t s_lo,
-                                             uint32_t s_hi, Acc &A, uint2 *dq = nullptr,
+                                             uint32_t s_hi, Acc &A, uint32_t *dq = nullptr,
                                              uint32_t *wacc = nullptr, const TaskTab *tt = nullptr)
 {
     if (P.oi == 0) run_phase<G, 0, THREADS, BLOCKED>(lat, g, P, thr, f, s_lo, s_hi, A, dq, wacc, tt);
@@ -600,7 +600,7 @@ __host__ __device__ __forceinline__ int band_table_rows(int H, int K)
 
 __host__ __device__ __forceinline__ long long band_table_offset(int H, int K, int RWb)
 {
-    return (long long)(H + 2 * (2 * K + 1)) * RWb + (long long)kBandThreads / 32 * kDrawQueue * 2;
+    return (long long)(H + 2 * (2 * K + 1)) * RWb + (long long)kBandThreads / 32 * kDrawQueueWords;
 }
 
 // Waits for phase `parity` of the mbarrier at shared address mbar, giving up after
@@ -749,7 +749,7 @@ band_phases_kernel(const SweepJob J, const void *__restrict__ src, void *__restr
 
     Acc A = {0u, 0u, 0u, 0u, 0};
     // the warps' draw queues follow the rows (H + 2D rows of the tallest band)
-    uint2 *const dq = (uint2 *)(smem + (size_t)(H + 2 * g.D) * RWb) + (size_t)(tid >> 5) * kDrawQueue;
+    uint32_t *const dq = smem + (size_t)(H + 2 * g.D) * RWb + (size_t)(tid >> 5) * kDrawQueueWords;
     uint32_t *const wacc = wacc_all + (tid & ~31);
     for (int j = 0; j < K; ++j) {
         const PhaseR P = pp[j];
