@@ -227,6 +227,15 @@ klmc_status klmc_cluster_histogram_noalloc(const void *dev_lattice, int32_t pack
 /* Counters (see klmc_counters).  Synchronises.  KLMC_ETIMEOUT as klmc_energy. */
 klmc_status klmc_get_counters(klmc_ctx *c, klmc_counters *out);
 
+/* Test hook for the bounded waits (0 in normal use).  From the next sweep on, each
+ * tiled launch of this handle that moves its rows by bulk copies expects `bytes`
+ * more than its copies deliver, so that its wait for them gives up after a short
+ * bound; the launch then leaves its band unwritten and klmc_energy /
+ * klmc_get_counters report KLMC_ETIMEOUT.  The handle's lattice is then no longer
+ * a state of the chain; other handles are unaffected.  Synchronises.  EINVAL for
+ * bytes < 0. */
+klmc_status klmc_test_copy_shortfall(klmc_ctx *c, int32_t bytes);
+
 /* Copies the lattice to host memory, one byte per site (n must equal Lx*Ly).
  * Synchronises. */
 klmc_status klmc_get_lattice(klmc_ctx *c, uint8_t *host_out, int64_t n);

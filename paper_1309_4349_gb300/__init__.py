@@ -109,6 +109,7 @@ def lib():
         "klmc_cluster_histogram": [vp, i32, vp, vp, i64, P(i64)],
         "klmc_cluster_histogram_device": [vp, i32, vp, vp, i64, vp],
         "klmc_get_counters": [vp, P(Counters)],
+        "klmc_test_copy_shortfall": [vp, i32],
         "klmc_get_lattice": [vp, vp, i64],
         "klmc_set_lattice": [vp, vp, i64, i64],
         "klmc_set_lattice_device": [vp, vp, i64, i64],
@@ -325,6 +326,11 @@ class Lattice:
         c = Counters()
         _check(lib().klmc_get_counters(self._h, ctypes.byref(c)))
         return c.as_dict()
+
+    def test_copy_shortfall(self, nbytes: int):
+        """Test hook: make this handle's tiled launches wait for row copies that
+        never arrive (klmc_test_copy_shortfall)."""
+        _check(lib().klmc_test_copy_shortfall(self._h, int(nbytes)))
 
     def get_lattice(self) -> np.ndarray:
         out = np.zeros(self.N, dtype=np.uint8)

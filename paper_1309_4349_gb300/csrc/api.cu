@@ -775,6 +775,17 @@ klmc_status klmc_cluster_histogram(klmc_ctx *c, int32_t species, int64_t *sizes,
     return KLMC_OK;
 }
 
+klmc_status klmc_test_copy_shortfall(klmc_ctx *c, int32_t bytes)
+{
+    if (!c) return fail(KLMC_EINVAL, "ctx is NULL");
+    if (bytes < 0) return fail(KLMC_EINVAL, "bytes must be >= 0");
+    KLMC_CUDA(cudaStreamSynchronize(c->stream));
+    c->job.copy_shortfall = bytes;
+    for (auto &g : c->graphs) cudaGraphExecDestroy(g.second);  // they hold the old value
+    c->graphs.clear();
+    return KLMC_OK;
+}
+
 klmc_status klmc_get_counters(klmc_ctx *c, klmc_counters *out)
 {
     if (!c || !out) return fail(KLMC_EINVAL, "NULL argument");

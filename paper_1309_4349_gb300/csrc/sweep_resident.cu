@@ -620,6 +620,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, int li
 }
 
 constexpr int kCopyWaitPolls = 1 << 20;
+constexpr int kCopyWaitPollsShort = 1 << 12;  // under the test hook (SweepJob::copy_shortfall)
 
 // Tiled path, blocked: bands of H rows of a lattice too large for a cluster's
 // shared memory, one CTA each, K phases per launch.  A CTA loads its band and
@@ -689,7 +690,8 @@ band_phases_kernel(const SweepJob J, const void *__restrict__ src, void *__restr
             if (tid == 0) {
                 unsigned long long st;
                 asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 %0, [%1], %2;"
-                             : "=l"(st) : "r"(bar), "r"(row_bytes * (uint32_t)NL) : "memory");
+                             : "=l"(st) : "r"(bar), "r"(row_bytes * (uint32_t)NL + (uint32_t)J.copy_shortfall)
+                             : "memory");
             }
             __syncwarp();
             for (int lr = tid; lr < NL; lr += 32) {
@@ -703,12 +705,13 @@ band_phases_kernel(const SweepJob J, const void *__restrict__ src, void *__restr
                     ::"r"(to), "l"(from), "r"(row_bytes), "r"(bar) : "memory");
             }
         }
-        const bool ok = mbar_wait(bar, 0u, kCopyWaitPolls);
+        const int polls = J.copy_shortfall != 0 ? kCopyWaitPollsShort : kCopyWaitPolls;
+        const bool ok = mbar_wait(bar, 0u, polls);
         if (__syncthreads_or(!ok)) {
             // Give up on this launch: report it, let the copies in flight land, and
             // leave the band unwritten.
             if (tid == 0) atomicExch((unsigned long long *)&J.state[kFault], 1ull);
-            mbar_wait(bar, 0u, kCopyWaitPolls);
+            mbar_wait(bar, 0u, polls);
             return;
         }
         for (int lr = tid; lr < NL; lr += THREADS) {
