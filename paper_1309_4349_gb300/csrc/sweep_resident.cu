@@ -212,6 +212,9 @@ __device__ __forceinline__ void run_phase(const uint32_t *lat, const Geo &g, con
 {
     // b = a + o: (1,0) -> same row, +1; (0,1) -> next row; (1,-1) -> previous row, +1
     constexpr int bdy = OI == 0 ? 0 : (OI == 1 ? 1 : -1);
+    // Interior words flip without the row-end checks in the issue-bound band kernel
+    // (1024 threads); in the resident kernels (128 registers) the extra code costs more.
+    constexpr bool kFlipFast = THREADS == 1024;
     constexpr int bdx = OI == 1 ? 0 : 1;
     const int lane = threadIdx.x & 31;
     const int H = g.Y1 - g.Y0;
@@ -291,7 +294,20 @@ __device__ __forceinline__ void run_phase(const uint32_t *lat, const Geo &g, con
                     wrap0 = true;
                 }
             }
-            if (BLOCKED) {
+            if (kFlipFast && BLOCKED && j != 0 && 32 * j + 65 <= g.Lx) {
+                // a word clear of both row ends: no pad copies, no wrap, exact words
+                const uint32_t rowbytes = 4u * (uint32_t)g.RW;
+                const uint32_t wa = g.lat_addr + rowbytes * (uint32_t)lr + 4u * (uint32_t)(j + 1);
+                const uint32_t wb = wa + rowbytes * (uint32_t)bdy;
+                const uint32_t lo = (uint32_t)mb, hi = (uint32_t)(mb >> 32);
+                if (bdy == 0) {
+                    xor_word(wa, 0u, true, acc | lo);
+                } else {
+                    xor_word(wa, 0u, true, acc);
+                    xor_word(wb, 0u, true, lo);
+                }
+                xor_word(wb + 4u, 0u, true, hi);
+            } else if (BLOCKED) {
                 const uint32_t rowbytes = 4u * (uint32_t)g.RW;
                 const uint32_t ra = g.lat_addr + rowbytes * (uint32_t)lr;
                 const uint32_t rb = g.lat_addr + rowbytes * (uint32_t)(lr + bdy);
