@@ -247,7 +247,7 @@ def run_reference(args, rank, world=1):
 
 
 # ---------------------------------------------------------------------------
-# Other workloads (the default driver line is the 400x400 x 5 omega workload).
+# Other workloads (the default line is the 400x400 x 5 omega workload).
 # ---------------------------------------------------------------------------
 C1 = dict(L=64, n_A=2048, omega=0.6, seed=1, mcs=1000, hist_every=100)
 C3 = dict(L=8192, omega=0.85, seed=7, mcs=1000, trace_every=10)
