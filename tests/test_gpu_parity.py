@@ -493,3 +493,32 @@ def test_full_size_400_sampled():
     assert np.array_equal(lat.get_lattice(), ref.lattice)
     assert lat.energy()[0] == ref.n_unlike
     _hist_equal(lat, ref.lattice, 1)
+
+
+def test_c4_workload_sampled():
+    """The batched workload as the benchmark builds it (256 replicas, sides 100 to
+    1017, in one batch at the throughput shapes), for 12 MCS: every replica keeps
+    its composition and an energy equal to a recount, and the largest, the
+    smallest and two more replicas equal their oracle runs bit for bit."""
+    import bench
+
+    reps = bench.c4_replicas()
+    assert len(reps) == 256
+    b = klmc.Batch(reps)
+    n = 12
+    b.sweep([n] * len(reps))
+    sides = [r["Lx"] for r in reps]
+    for i, r in enumerate(reps):
+        lat = b.replicas[i]
+        t = lat.get_lattice()
+        assert int(t.sum()) == oracle.n_A(r["Lx"], r["Ly"], -1, r["fraction_A"]), i
+        assert lat.energy()[0] == lat.energy_recount(), i
+        c = lat.counters()
+        assert c["attempts"] <= n * r["Lx"] * r["Ly"] and c["accepts"] <= c["unlike"], i
+    for i in sorted({int(np.argmax(sides)), int(np.argmin(sides)), 17, 200}):
+        r = reps[i]
+        nA = oracle.n_A(r["Lx"], r["Ly"], -1, r["fraction_A"])
+        ref = oracle.run(r["Lx"], r["Ly"], klmc.TRI6, r["omega_over_kT"], r["seed"],
+                         oracle.init(r["Lx"], r["Ly"], nA, r["seed"]), 0, n)
+        assert_same_run(b.replicas[i], ref)
+    b.close()
