@@ -63,6 +63,19 @@ def test_helical_traced_and_large():
     assert_same_run(lat, ref, Lx, Ly)
 
 
+def test_helical_large():
+    """8195 x 3129 (2.6e7 sites, 7 | N, Lx mod 7 = 5): two steps equal the
+    oracle's."""
+    Lx, Ly, bw, seed = 8195, 3129, 0.8, 21
+    assert oracle.helical_valid(Lx, Ly)
+    nA = Lx * Ly * 2 // 5
+    lat = make(Lx, Ly, nA, bw, seed)
+    t0 = lat.get_lattice()
+    lat.sweep(2)
+    ref = oracle.run_mpkk(Lx, Ly, bw, seed, t0, 0, 2)
+    assert_same_run(lat, ref, Lx, Ly)
+
+
 def test_helical_set_lattice_and_histograms():
     Lx, Ly = 31, 14
     lat = make(Lx, Ly, 100, 1.1, 3)
