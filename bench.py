@@ -786,7 +786,10 @@ def main():
                 "peak_basis": (f"{sm_count} SMs x {INT32_LANES_PER_SM} INT32 lanes/clk x median SM "
                                f"clock {sm_mhz:.0f} MHz (derived; probes/int_peak.cu)"),
                 "frac_of_occupied_sms": achieved_tops / (peak_tops * min(ctas, sm_count) / sm_count),
-                "sweep_share_of_step": sum(sweep_ms) / sum(ms_steps)}
+                "sweep_share_of_step": sum(sweep_ms) / sum(ms_steps),
+                "note": "latency-bound: each phase waits for its slowest task (the lane with the most Philox "
+                        "draws) and a barrier; the 5 lattices occupy 5 clusters of SMs (profiles/"
+                        "resident_sweep_400x400x5_ncu.md: issue active 30%, top stall barrier)"}
 
     # Exactness spot check of the timed state (the parity tests do the full check).
     e_run = [lat.energy()[0] for lat in batch.replicas]
