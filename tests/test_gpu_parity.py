@@ -522,3 +522,29 @@ def test_c4_workload_sampled():
                          oracle.init(r["Lx"], r["Ly"], nA, r["seed"]), 0, n)
         assert_same_run(b.replicas[i], ref)
     b.close()
+
+
+def test_c1_workload_full():
+    """The 64x64 workload as the benchmark runs it (TRI6, byte store, 2048 A, omega/kT
+    0.6, seed 1, tuned launch shape, 1000 MCS with an A-cluster histogram every 100
+    MCS), in full: all ten histograms, the final lattice, the counters and the
+    energy equal the oracle's."""
+    import bench
+
+    c = bench.C1
+    L = c["L"]
+    lat = klmc.Lattice(L, L, n_A=c["n_A"], omega_over_kT=c["omega"], seed=c["seed"], packing=klmc.PACK_BYTE)
+    lat.autotune(16)
+    t = oracle.init(L, L, c["n_A"], c["seed"])
+    assert np.array_equal(lat.get_lattice(), t)
+    nu, cnt = None, (0, 0, 0, 0)
+    for k in range(c["mcs"] // c["hist_every"]):
+        lat.sweep(c["hist_every"])
+        r = oracle.run(L, L, klmc.TRI6, c["omega"], c["seed"], t, k * c["hist_every"], c["hist_every"],
+                       n_unlike0=nu, counters0=cnt)
+        t, nu, cnt = r.lattice, r.n_unlike, r.counters()
+        sizes, counts = lat.cluster_histogram(1)
+        rs, rc = oracle.cluster_histogram(L, L, klmc.TRI6, t, 1)
+        assert np.array_equal(np.asarray(sizes), rs) and np.array_equal(np.asarray(counts), rc), k
+    assert_same_run(lat, r)
+    lat.close()
