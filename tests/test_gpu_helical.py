@@ -103,3 +103,30 @@ def test_helical_rejections():
     with pytest.raises(klmc.KlmcError) as e:
         klmc.Batch([dict(Lx=10, Ly=7, boundary=klmc.HELICAL)])
     assert e.value.status == 1
+
+
+def test_c6_workload_one_run_full():
+    """One of the helical workload's five runs as the benchmark sets it up (402 x
+    399, 30% A, omega/kT 0.6, its seed) for the full 2000 MCS: the A-cluster
+    histogram after every 500 MCS, the final lattice, the counters and the energy
+    equal the oracle's."""
+    import bench
+
+    c = bench.C6
+    Lx, Ly = c["Lx"], c["Ly"]
+    w, seed = bench.OMEGAS[2], bench.SEEDS[2]
+    lat = klmc.Lattice(Lx, Ly, fraction_A=bench.FRACTION_A, omega_over_kT=w, seed=seed, boundary=klmc.HELICAL)
+    nA = oracle.n_A(Lx, Ly, -1, bench.FRACTION_A)
+    t = oracle.init(Lx, Ly, nA, seed)
+    assert np.array_equal(lat.get_lattice(), t)
+    nu, cnt = None, (0, 0, 0, 0)
+    for k in range(c["mcs"] // c["hist_every"]):
+        lat.sweep(c["hist_every"])
+        r = oracle.run_mpkk(Lx, Ly, w, seed, t, k * c["hist_every"], c["hist_every"], n_unlike0=nu,
+                            counters0=cnt)
+        t, nu, cnt = r.lattice, r.n_unlike, r.counters()
+        sizes, counts = lat.cluster_histogram(1)
+        rs, rc = oracle.cluster_histogram(Lx, Ly, oracle.TRI6, t, 1, oracle.HELICAL)
+        assert np.array_equal(np.asarray(sizes), rs) and np.array_equal(np.asarray(counts), rc), k
+    assert_same_run(lat, r, Lx, Ly)
+    lat.close()
