@@ -380,26 +380,31 @@ __device__ __forceinline__ uint32_t draw_accepts(uint32_t dmask, const Planes &S
     return acc;
 }
 
-// Accept bits of this lane's dmask when the warp's draws are drawn by all its
-// lanes.  Every lane stores its S planes and first site index once, and appends
-// its draws (lane, bit) as 16-bit entries to the warp's queue at its prefix-sum
-// offset; then lane i draws entries i and i + 32 of every 64 (two Philox chains
-// interleaved), reading the entry's S and site from its owner's record, and
-// returns accepted bits to their lanes through wacc (the warp's 32 words of shared
-// memory, zero on entry and on return).  When the warp has more than kDrawQueue
-// draws, each lane draws its own.  Every lane of the warp must call it.
-// The warp's region q (16-byte aligned, kDrawQueueWords words): planes uint4[32],
-// sites uint32[32], entries uint16[kDrawQueue].
-constexpr int kDrawQueue = 256;
-constexpr int kDrawQueueWords = 32 * 4 + 32 + kDrawQueue / 2;
+// Accept bits of two tasks per lane (t and t + THREADS) when the warp's draws are
+// drawn by all its lanes.  Every lane stores each task's S planes and first site
+// index once, and appends its draws (task, lane, bit) as 16-bit entries to the
+// warp's queue at its prefix-sum offset; then lane i draws entries i and i + 32 of
+// every 64 (two Philox chains interleaved), reading the entry's S and site from
+// its record, and returns accepted bits through the warp's accept words with
+// shared atomics.  One scan and one pass serve both tasks, so a pass drains about
+// twice the draws of one task per lane.  When the warp has more than kDrawQueue2
+// draws, each lane draws its own.  Every lane of the warp must call it.  Region q
+// (16-byte aligned, kDrawQueue2Words words): planes uint4[2][32], sites
+// uint32[2][32], accept words uint32[2][32] (zero on entry and on return),
+// entries uint16[kDrawQueue2].
+constexpr int kDrawQueue2 = 512;
+constexpr int kDrawQueue2Words = 2 * 32 * 4 + 2 * 32 + 2 * 32 + kDrawQueue2 / 2;
 
-__device__ __forceinline__ uint32_t draw_accepts_queue(uint32_t dmask, const Planes &S, uint32_t site_base,
-                                                       const DrawKey &dk, const uint64_t *thr, uint32_t *q,
-                                                       uint32_t *wacc)
+__device__ __forceinline__ void draw_accepts_queue2(uint32_t dmask0, const Planes &S0, uint32_t base0,
+                                                    uint32_t dmask1, const Planes &S1, uint32_t base1,
+                                                    const DrawKey &dk, const uint64_t *thr, uint32_t *q,
+                                                    uint32_t &acc0, uint32_t &acc1)
 {
-    if (!__any_sync(0xFFFFFFFFu, dmask != 0u)) return 0u;
+    acc0 = 0u;
+    acc1 = 0u;
+    if (!__any_sync(0xFFFFFFFFu, (dmask0 | dmask1) != 0u)) return;
     const int lane = (int)(threadIdx.x & 31);
-    const int nd = __popc(dmask);
+    const int nd0 = __popc(dmask0), nd = nd0 + __popc(dmask1);
     int incl = nd;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -407,43 +412,58 @@ __device__ __forceinline__ uint32_t draw_accepts_queue(uint32_t dmask, const Pla
         if (lane >= o) incl += v;
     }
     const int total = __shfl_sync(0xFFFFFFFFu, incl, 31);
-    if (total > kDrawQueue) return draw_accepts(dmask, S, site_base, dk, thr);
-    uint4 *const planes = (uint4 *)q;
-    uint32_t *const sites = (uint32_t *)(planes + 32);
-    uint16_t *const ent = (uint16_t *)(sites + 32);
-    if (nd != 0) {
-        planes[lane] = make_uint4(S.s0, S.s1, S.s2, S.s3);
-        sites[lane] = site_base;
+    if (total > kDrawQueue2) {
+        acc0 = draw_accepts(dmask0, S0, base0, dk, thr);
+        acc1 = draw_accepts(dmask1, S1, base1, dk, thr);
+        return;
+    }
+    uint4 *const planes = (uint4 *)q;                  // [2][32]
+    uint32_t *const sites = (uint32_t *)(planes + 64);  // [2][32]
+    uint32_t *const wacc = sites + 64;                  // [2][32]
+    uint16_t *const ent = (uint16_t *)(wacc + 64);
+    if (dmask0 != 0u) {
+        planes[lane] = make_uint4(S0.s0, S0.s1, S0.s2, S0.s3);
+        sites[lane] = base0;
+    }
+    if (dmask1 != 0u) {
+        planes[32 + lane] = make_uint4(S1.s0, S1.s1, S1.s2, S1.s3);
+        sites[32 + lane] = base1;
     }
     int slot = incl - nd;
-    const uint32_t tag = (uint32_t)lane << 5;
-    uint32_t dm = dmask;
+    uint32_t dm = dmask0;
     while (dm != 0u) {
         const int p = __ffs(dm) - 1;
         dm &= dm - 1u;
-        ent[slot++] = (uint16_t)(tag | (uint32_t)p);
+        ent[slot++] = (uint16_t)(((uint32_t)lane << 5) | (uint32_t)p);
+    }
+    dm = dmask1;
+    while (dm != 0u) {
+        const int p = __ffs(dm) - 1;
+        dm &= dm - 1u;
+        ent[slot++] = (uint16_t)(1024u | ((uint32_t)lane << 5) | (uint32_t)p);
     }
     __syncwarp();
     for (int k = lane; k < total; k += 64) {
         const uint32_t e1 = ent[k];
         const bool two = k + 32 < total;
         const uint32_t e2 = two ? ent[k + 32] : e1;
-        const uint32_t l1 = e1 >> 5, p1 = e1 & 31u, l2 = e2 >> 5, p2 = e2 & 31u;
+        const uint32_t r1i = e1 >> 5, p1 = e1 & 31u, r2i = e2 >> 5, p2 = e2 & 31u;  // record = task*32 + lane
         uint32_t r1, r2;
-        philox2_w0_key(sites[l1] + p1, sites[l2] + p2, dk, r1, r2);
-        const uint4 a = planes[l1], b = planes[l2];
-        const uint32_t S1 = ((a.x >> p1) & 1u) | (((a.y >> p1) & 1u) << 1) | (((a.z >> p1) & 1u) << 2) |
+        philox2_w0_key(sites[r1i] + p1, sites[r2i] + p2, dk, r1, r2);
+        const uint4 a = planes[r1i], b = planes[r2i];
+        const uint32_t Sa = ((a.x >> p1) & 1u) | (((a.y >> p1) & 1u) << 1) | (((a.z >> p1) & 1u) << 2) |
                             (((a.w >> p1) & 1u) << 3);
-        const uint32_t S2 = ((b.x >> p2) & 1u) | (((b.y >> p2) & 1u) << 1) | (((b.z >> p2) & 1u) << 2) |
+        const uint32_t Sb = ((b.x >> p2) & 1u) | (((b.y >> p2) & 1u) << 1) | (((b.z >> p2) & 1u) << 2) |
                             (((b.w >> p2) & 1u) << 3);
-        if ((uint64_t)r1 < thr[S1]) atomicOr(wacc + l1, 1u << p1);
-        if (two && (uint64_t)r2 < thr[S2]) atomicOr(wacc + l2, 1u << p2);
+        if ((uint64_t)r1 < thr[Sa]) atomicOr(wacc + r1i, 1u << p1);
+        if (two && (uint64_t)r2 < thr[Sb]) atomicOr(wacc + r2i, 1u << p2);
     }
     __syncwarp();
-    const uint32_t acc = wacc[lane];
+    acc0 = wacc[lane];
+    acc1 = wacc[32 + lane];
     wacc[lane] = 0u;
+    wacc[32 + lane] = 0u;
     __syncwarp();
-    return acc;
 }
 
 // One padded shared-memory row from the device store (see the row layout above):

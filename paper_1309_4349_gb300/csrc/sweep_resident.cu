@@ -207,14 +207,10 @@ __device__ __forceinline__ void build_task_table(const PhaseR &P, const Geo &g, 
 template <int G, int OI, int THREADS, bool BLOCKED>
 __device__ __forceinline__ void run_phase(const uint32_t *lat, const Geo &g, const PhaseR &P,
                                           const uint64_t *thr, int f,
-                                          uint32_t s_lo, uint32_t s_hi, Acc &A, uint32_t *dq = nullptr,
-                                          uint32_t *wacc = nullptr, const TaskTab *tt = nullptr)
+                                          uint32_t s_lo, uint32_t s_hi, Acc &A, const TaskTab *tt = nullptr)
 {
     // b = a + o: (1,0) -> same row, +1; (0,1) -> next row; (1,-1) -> previous row, +1
     constexpr int bdy = OI == 0 ? 0 : (OI == 1 ? 1 : -1);
-    // Interior words flip without the row-end checks in the issue-bound band kernel
-    // (1024 threads); in the resident kernels (128 registers) the extra code costs more.
-    constexpr bool kFlipFast = THREADS == 1024;
     constexpr int bdx = OI == 1 ? 0 : 1;
     const int lane = threadIdx.x & 31;
     const int H = g.Y1 - g.Y0;
@@ -265,10 +261,7 @@ __device__ __forceinline__ void run_phase(const uint32_t *lat, const Geo &g, con
         const uint32_t dmask = unl & draw_positions<G>(S, g.sign);
         uint32_t acc = unl & ~dmask;
 
-        if (dq != nullptr)
-            acc |= draw_accepts_queue(dmask, S, (uint32_t)(ybase + x0), dk, thr, dq, wacc);
-        else
-            acc |= draw_accepts(dmask, S, (uint32_t)(ybase + x0), dk, thr);
+        acc |= draw_accepts(dmask, S, (uint32_t)(ybase + x0), dk, thr);
         const bool own = !BLOCKED || (unsigned)(lr - g.D) < (unsigned)H;
         if (own) {
             A.att += __popc(am);
@@ -294,20 +287,7 @@ __device__ __forceinline__ void run_phase(const uint32_t *lat, const Geo &g, con
                     wrap0 = true;
                 }
             }
-            if (kFlipFast && BLOCKED && j != 0 && 32 * j + 65 <= g.Lx) {
-                // a word clear of both row ends: no pad copies, no wrap, exact words
-                const uint32_t rowbytes = 4u * (uint32_t)g.RW;
-                const uint32_t wa = g.lat_addr + rowbytes * (uint32_t)lr + 4u * (uint32_t)(j + 1);
-                const uint32_t wb = wa + rowbytes * (uint32_t)bdy;
-                const uint32_t lo = (uint32_t)mb, hi = (uint32_t)(mb >> 32);
-                if (bdy == 0) {
-                    xor_word(wa, 0u, true, acc | lo);
-                } else {
-                    xor_word(wa, 0u, true, acc);
-                    xor_word(wb, 0u, true, lo);
-                }
-                xor_word(wb + 4u, 0u, true, hi);
-            } else if (BLOCKED) {
+            if (BLOCKED) {
                 const uint32_t rowbytes = 4u * (uint32_t)g.RW;
                 const uint32_t ra = g.lat_addr + rowbytes * (uint32_t)lr;
                 const uint32_t rb = g.lat_addr + rowbytes * (uint32_t)(lr + bdy);
@@ -332,15 +312,147 @@ __device__ __forceinline__ void run_phase(const uint32_t *lat, const Geo &g, con
     }
 }
 
+// Band kernel: one phase with two tasks per lane (t and t + THREADS) sharing one
+// pass of the warp's draw queue.  Blocked (all flips local, only the band's anchors
+// counted), with the phase's task table when it fits.
+struct TaskPrep {
+    uint32_t dmask, acc;  // positions that need a draw; accepted without one
+    Planes S;
+    uint32_t base;        // site index of position 0
+    int lr, j;
+    bool own;
+};
+
+template <int G, int OI>
+__device__ __forceinline__ void band_task_prep(const uint32_t *lat, const Geo &g, const PhaseR &P, bool use_tab,
+                                               const TaskTab *tt, int t, bool valid, TaskPrep &T, Acc &A)
+{
+    uint32_t am = 0u, ta = 0u, tb = 0u;
+    Planes S = {0u, 0u, 0u, 0u};
+    int ybase = 0, j = 0, lr = 0;
+    if (valid) {
+        const int mi = (int)(((unsigned long long)t * g.magicW) >> 32);
+        j = t - mi * g.W;
+        if (use_tab) {
+            const int2 r = tt->row[mi];
+            lr = r.x;
+            ybase = r.y;
+            am = tt->am[j];
+        } else {
+            const int m = mi < P.c[0] ? P.a[0] + mi
+                        : (mi < P.c[1] ? P.a[1] + mi : (mi < P.c[2] ? P.a[2] + mi : P.a[3] + mi));
+            int y = P.ry + P.py * m;
+            if (y >= g.Ly) y -= g.Ly;
+            lr = y - g.base;
+            if (lr < 0) lr += g.Ly;
+            ybase = y * g.Lx;
+            am = anchor_mask(j << 5, P, g.Lx);
+        }
+        evaluate<G, OI>(lat + (size_t)lr * g.RW, g.RW, j, ta, tb, S);
+    }
+    const uint32_t unl = (ta ^ tb) & am;
+    T.dmask = unl & draw_positions<G>(S, g.sign);
+    T.acc = unl & ~T.dmask;
+    T.S = S;
+    T.base = (uint32_t)(ybase + (j << 5));
+    T.lr = lr;
+    T.j = j;
+    T.own = (unsigned)(lr - g.D) < (unsigned)(g.Y1 - g.Y0);
+    if (T.own) {
+        A.att += __popc(am);
+        A.unl += __popc(unl);
+        A.drw += __popc(T.dmask);
+    }
+}
+
+template <int OI>
+__device__ __forceinline__ void band_task_finish(const Geo &g, const TaskPrep &T, uint32_t acc, Acc &A)
+{
+    constexpr int bdy = OI == 0 ? 0 : (OI == 1 ? 1 : -1);
+    constexpr int bdx = OI == 1 ? 0 : 1;
+    if (!acc) return;
+    if (T.own) {
+        const int na = __popc(acc);
+        A.acc += na;
+        const int sum_s = __popc(T.S.s0 & acc) + 2 * __popc(T.S.s1 & acc) + 4 * __popc(T.S.s2 & acc) +
+                          8 * __popc(T.S.s3 & acc);
+        A.dn += 2 * (sum_s - g.zm1 * na);
+    }
+    const int j = T.j, lr = T.lr, x0 = j << 5;
+    unsigned long long mb = (unsigned long long)acc << bdx;
+    bool wrap0 = false;
+    if (bdx == 1) {
+        const int wb = g.Lx - x0;
+        if (wb <= 32 && ((mb >> wb) & 1ull)) {
+            mb &= ~(1ull << wb);
+            wrap0 = true;
+        }
+    }
+    const uint32_t rowbytes = 4u * (uint32_t)g.RW;
+    if (j != 0 && 32 * j + 65 <= g.Lx) {
+        // a word clear of both row ends: no pad copies, no wrap, exact words
+        const uint32_t wa = g.lat_addr + rowbytes * (uint32_t)lr + 4u * (uint32_t)(j + 1);
+        const uint32_t wbw = wa + rowbytes * (uint32_t)bdy;
+        const uint32_t lo = (uint32_t)mb, hi = (uint32_t)(mb >> 32);
+        if (bdy == 0) {
+            xor_word(wa, 0u, true, acc | lo);
+        } else {
+            xor_word(wa, 0u, true, acc);
+            xor_word(wbw, 0u, true, lo);
+        }
+        xor_word(wbw + 4u, 0u, true, hi);
+        return;
+    }
+    const uint32_t ra = g.lat_addr + rowbytes * (uint32_t)lr;
+    const uint32_t rb = g.lat_addr + rowbytes * (uint32_t)(lr + bdy);
+    if (bdy == 0) {
+        flip_row(g, ra, j, (unsigned long long)acc | mb, 0u, true);
+    } else {
+        flip_row(g, ra, j, (unsigned long long)acc, 0u, true);
+        flip_row(g, rb, j, mb, 0u, true);
+    }
+    if (wrap0) flip_row(g, rb, 0, 1ull, 0u, true);
+}
+
+template <int G, int OI, int THREADS>
+__device__ __forceinline__ void run_phase_pair(const uint32_t *lat, const Geo &g, const PhaseR &P,
+                                               const uint64_t *thr, int f, uint32_t s_lo, uint32_t s_hi,
+                                               Acc &A, uint32_t *q, const TaskTab *tt)
+{
+    const int lane = threadIdx.x & 31;
+    const int ntask = P.ntask;
+    const bool use_tab = tt != nullptr && table_fits(g, P, *tt);
+    const DrawKey dk = draw_key((uint32_t)f, s_lo, s_hi, g.k0, g.k1);
+    for (int t0 = threadIdx.x & ~31; t0 < ntask; t0 += 2 * THREADS) {
+        const int ta = t0 + lane, tb = t0 + THREADS + lane;
+        TaskPrep T0, T1;
+        band_task_prep<G, OI>(lat, g, P, use_tab, tt, ta, ta < ntask, T0, A);
+        band_task_prep<G, OI>(lat, g, P, use_tab, tt, tb, tb < ntask, T1, A);
+        uint32_t a0, a1;
+        draw_accepts_queue2(T0.dmask, T0.S, T0.base, T1.dmask, T1.S, T1.base, dk, thr, q, a0, a1);
+        band_task_finish<OI>(g, T0, T0.acc | a0, A);
+        band_task_finish<OI>(g, T1, T1.acc | a1, A);
+    }
+}
+
+template <int G, int THREADS>
+__device__ __forceinline__ void run_phase_pair_oi(const uint32_t *lat, const Geo &g, const PhaseR &P,
+                                                  const uint64_t *thr, int f, uint32_t s_lo, uint32_t s_hi,
+                                                  Acc &A, uint32_t *q, const TaskTab *tt)
+{
+    if (P.oi == 0) run_phase_pair<G, 0, THREADS>(lat, g, P, thr, f, s_lo, s_hi, A, q, tt);
+    else if (G == kTRI6 && P.oi == 2) run_phase_pair<G, 2, THREADS>(lat, g, P, thr, f, s_lo, s_hi, A, q, tt);
+    else run_phase_pair<G, 1, THREADS>(lat, g, P, thr, f, s_lo, s_hi, A, q, tt);
+}
+
 template <int G, int THREADS, bool BLOCKED>
 __device__ __forceinline__ void run_phase_oi(const uint32_t *lat, const Geo &g, const PhaseR &P,
                                              const uint64_t *thr, int f, uint32_t s_lo,
-                                             uint32_t s_hi, Acc &A, uint32_t *dq = nullptr,
-                                             uint32_t *wacc = nullptr, const TaskTab *tt = nullptr)
+                                             uint32_t s_hi, Acc &A, const TaskTab *tt = nullptr)
 {
-    if (P.oi == 0) run_phase<G, 0, THREADS, BLOCKED>(lat, g, P, thr, f, s_lo, s_hi, A, dq, wacc, tt);
-    else if (G == kTRI6 && P.oi == 2) run_phase<G, 2, THREADS, BLOCKED>(lat, g, P, thr, f, s_lo, s_hi, A, dq, wacc, tt);
-    else run_phase<G, 1, THREADS, BLOCKED>(lat, g, P, thr, f, s_lo, s_hi, A, dq, wacc, tt);
+    if (P.oi == 0) run_phase<G, 0, THREADS, BLOCKED>(lat, g, P, thr, f, s_lo, s_hi, A, tt);
+    else if (G == kTRI6 && P.oi == 2) run_phase<G, 2, THREADS, BLOCKED>(lat, g, P, thr, f, s_lo, s_hi, A, tt);
+    else run_phase<G, 1, THREADS, BLOCKED>(lat, g, P, thr, f, s_lo, s_hi, A, tt);
 }
 
 template <typename T>
@@ -530,9 +642,9 @@ resident_sweep_kernel(const SweepJob *__restrict__ jobs, const SweepCall *__rest
             const TaskTab *tt = &Tc;
             if (blocked) {
                 if (J.geometry == kTRI6)
-                    run_phase_oi<kTRI6, THREADS, true>(lat, g, P, thr, f, s_lo, s_hi, A, nullptr, nullptr, tt);
+                    run_phase_oi<kTRI6, THREADS, true>(lat, g, P, thr, f, s_lo, s_hi, A, tt);
                 else
-                    run_phase_oi<kSQ4, THREADS, true>(lat, g, P, thr, f, s_lo, s_hi, A, nullptr, nullptr, tt);
+                    run_phase_oi<kSQ4, THREADS, true>(lat, g, P, thr, f, s_lo, s_hi, A, tt);
                 __syncthreads();
                 if (f % K == K - 1 && !(f == 7 && it + 1 == Cl.n_mcs)) {
                     exchange_halos<THREADS>(lat, g, hmax, block & 1);
@@ -540,9 +652,9 @@ resident_sweep_kernel(const SweepJob *__restrict__ jobs, const SweepCall *__rest
                 }
             } else {
                 if (J.geometry == kTRI6)
-                    run_phase_oi<kTRI6, THREADS, false>(lat, g, P, thr, f, s_lo, s_hi, A, nullptr, nullptr, tt);
+                    run_phase_oi<kTRI6, THREADS, false>(lat, g, P, thr, f, s_lo, s_hi, A, tt);
                 else
-                    run_phase_oi<kSQ4, THREADS, false>(lat, g, P, thr, f, s_lo, s_hi, A, nullptr, nullptr, tt);
+                    run_phase_oi<kSQ4, THREADS, false>(lat, g, P, thr, f, s_lo, s_hi, A, tt);
                 phase_barrier(C);
             }
         }
@@ -616,7 +728,7 @@ __host__ __device__ __forceinline__ int band_table_rows(int H, int K)
 
 __host__ __device__ __forceinline__ long long band_table_offset(int H, int K, int RWb)
 {
-    return (long long)(H + 2 * (2 * K + 1)) * RWb + (long long)kBandThreads / 32 * kDrawQueueWords;
+    return (long long)(H + 2 * (2 * K + 1)) * RWb + (long long)kBandThreads / 32 * kDrawQueue2Words;
 }
 
 // Waits for phase `parity` of the mbarrier at shared address mbar, giving up after
@@ -657,11 +769,9 @@ band_phases_kernel(const SweepJob J, const void *__restrict__ src, void *__restr
     __shared__ PhaseR pp[8];
     __shared__ uint64_t thr[16];
     __shared__ long long red[5][kWarps];
-    __shared__ uint32_t wacc_all[THREADS];  // per-warp accept words of queued draws
     __shared__ __align__(8) unsigned long long copy_bar;
     // The next launch may be scheduled now; it waits for this one before it reads.
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-    wacc_all[threadIdx.x] = 0u;
 
     Geo g;
     g.Lx = J.Lx; g.Ly = J.Ly; g.W = J.W; g.RW = band_row_words(J.W); g.magicW = J.magicW;
@@ -768,17 +878,18 @@ band_phases_kernel(const SweepJob J, const void *__restrict__ src, void *__restr
 
     Acc A = {0u, 0u, 0u, 0u, 0};
     // the warps' draw queues follow the rows (H + 2D rows of the tallest band)
-    uint32_t *const dq = smem + (size_t)(H + 2 * g.D) * RWb + (size_t)(tid >> 5) * kDrawQueueWords;
-    uint32_t *const wacc = wacc_all + (tid & ~31);
+    uint32_t *const dq = smem + (size_t)(H + 2 * g.D) * RWb + (size_t)(tid >> 5) * kDrawQueue2Words;
+    dq[2 * 32 * 4 + 2 * 32 + (tid & 31)] = 0u;       // the queue's accept words start at zero
+    dq[2 * 32 * 4 + 2 * 32 + 32 + (tid & 31)] = 0u;
     for (int j = 0; j < K; ++j) {
         const PhaseR P = pp[j];
         uint32_t *const t = tab_base + (size_t)j * (tab_w + 2 * tab_rows);
         const TaskTab T = {t, (int2 *)(t + tab_w), g.W, tab_rows};
         const TaskTab *const tt = tables ? &T : nullptr;
         if (J.geometry == kTRI6)
-            run_phase_oi<kTRI6, THREADS, true>(lat, g, P, thr, f0 + j, s_lo, s_hi, A, dq, wacc, tt);
+            run_phase_pair_oi<kTRI6, THREADS>(lat, g, P, thr, f0 + j, s_lo, s_hi, A, dq, tt);
         else
-            run_phase_oi<kSQ4, THREADS, true>(lat, g, P, thr, f0 + j, s_lo, s_hi, A, dq, wacc, tt);
+            run_phase_pair_oi<kSQ4, THREADS>(lat, g, P, thr, f0 + j, s_lo, s_hi, A, dq, tt);
         __syncthreads();
     }
 
