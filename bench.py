@@ -64,9 +64,9 @@ INT32_LANES_PER_SM = 64
 # of the 400x400 x 5 workload; profiles/band_phases_8192x8192_ncu.md: one 4-phase band
 # launch of the 8192x8192 lattice), valid only for the kernel sources they were taken
 # with (hash of sweep_resident.cu + sweep_common.cuh).
-TRAFFIC_C2_LAUNCH = 222464
-TRAFFIC_C3_LAUNCH = 8480256
-TRAFFIC_SOURCES = "f216659d09c9e827"
+TRAFFIC_C2_LAUNCH = 306432
+TRAFFIC_C3_LAUNCH = 8498432
+TRAFFIC_SOURCES = "1553ba35071005ba"
 
 
 
