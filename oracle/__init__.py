@@ -104,6 +104,8 @@ def _load():
     lib.orc_snapshot.restype = ctypes.c_int
     lib.orc_image_ffn.argtypes = [vp, vp, i32, i32, i32, u64, i64, ctypes.POINTER(i64)]
     lib.orc_image_ffn.restype = i64
+    lib.orc_cluster_averages.argtypes = [vp, vp, i64, ctypes.POINTER(dbl), ctypes.POINTER(dbl)]
+    lib.orc_cluster_averages.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -237,6 +239,30 @@ def cluster_histogram(Lx: int, Ly: int, geometry: int, t: np.ndarray, species: i
     counts = np.zeros(max(n, 1), dtype=np.int64)
     lib.orc_cluster_histogram_b(Lx, Ly, geometry, boundary, _ptr(t), species, _ptr(sizes), _ptr(counts), n)
     return sizes[:n], counts[:n]
+
+
+def histogram_averages(sizes, counts):
+    """(number average, weight average) of a sparse cluster-size histogram: sum s c
+    / sum c and sum s^2 c / sum s c, each one FP64 division of exact int64 sums
+    (section "Cluster Analysis" results: average cluster size; reading R14).  Both
+    are 0 for an empty histogram."""
+    sz = np.ascontiguousarray(np.asarray(sizes, dtype=np.int64))
+    ct = np.ascontiguousarray(np.asarray(counts, dtype=np.int64))
+    if sz.shape != ct.shape:
+        raise ValueError("sizes and counts differ in length")
+    a, b = ctypes.c_double(), ctypes.c_double()
+    rc = _load().orc_cluster_averages(_ptr(sz), _ptr(ct), sz.size, ctypes.byref(a), ctypes.byref(b))
+    if rc == -1:
+        raise ValueError("negative size or count")
+    if rc != 0:
+        raise OverflowError("histogram sums exceed int64")
+    return a.value, b.value
+
+
+def cluster_averages(Lx: int, Ly: int, geometry: int, t: np.ndarray, species: int = 1,
+                     boundary: int = PERIODIC):
+    """(number average, weight average) cluster size of the species' clusters."""
+    return histogram_averages(*cluster_histogram(Lx, Ly, geometry, t, species, boundary))
 
 
 # ---------------------------------------------------------------------------

@@ -79,6 +79,11 @@
  *      (0,-1), (1,-1), w = word (p mod 4) of Philox(seed, {p div 4, 0xFFFFFFFC,
  *      m_lo, m_hi}); it is similar iff that neighbour is a lattice pixel of the
  *      image whose gray level differs by at most delta (35 in the paper).
+ *   R14 average cluster size (section "Cluster Analysis" results, which plot
+ *      the average cluster size without naming the average): both the number
+ *      average sum s c / sum c and the weight average sum s^2 c / sum s c of the
+ *      sparse histogram, each one FP64 division of exact int64 sums; 0 when the
+ *      species has no site.
  */
 #include <math.h>
 #include <stdint.h>
@@ -662,6 +667,35 @@ int64_t orc_cluster_histogram(int Lx, int Ly, int geometry, const uint8_t *t, in
                               int64_t *sizes, int64_t *counts, int64_t capacity)
 {
     return orc_cluster_histogram_b(Lx, Ly, geometry, ORC_PERIODIC, t, species, sizes, counts, capacity);
+}
+
+/* Average cluster size (section "Cluster Analysis" results: the average size of
+ * the clusters over time) from a sparse histogram of n (size s_k, count c_k)
+ * pairs.  The three sums are exact integers; each average is one FP64 division
+ * of two of them:
+ *   number average <s>_n = sum_k s_k c_k   / sum_k c_k
+ *   weight average <s>_w = sum_k s_k^2 c_k / sum_k s_k c_k
+ * R14: both are 0 for an empty histogram (no site of the species).  Returns 0,
+ * -1 for a negative size or count, -2 when a sum would leave int64. */
+int orc_cluster_averages(const int64_t *sizes, const int64_t *counts, int64_t n, double *number_avg,
+                         double *weight_avg)
+{
+    int64_t n_clusters = 0, n_sites = 0, sum_sq = 0;
+    for (int64_t k = 0; k < n; ++k) {
+        int64_t s = sizes[k], c = counts[k];
+        if (s < 0 || c < 0) return -1;
+        if (s > 0 && c > INT64_MAX / s) return -2;
+        int64_t sc = s * c;
+        if (s > 0 && sc > INT64_MAX / s) return -2;
+        int64_t ssc = sc * s;
+        if (n_clusters > INT64_MAX - c || n_sites > INT64_MAX - sc || sum_sq > INT64_MAX - ssc) return -2;
+        n_clusters += c;
+        n_sites += sc;
+        sum_sq += ssc;
+    }
+    *number_avg = n_clusters > 0 ? (double)n_sites / (double)n_clusters : 0.0;
+    *weight_avg = n_sites > 0 ? (double)sum_sq / (double)n_sites : 0.0;
+    return 0;
 }
 
 /* ------------------------------------------------------------------------- */
