@@ -198,6 +198,25 @@ klmc_status klmc_cluster_histogram_device(klmc_ctx *c, int32_t species, int64_t 
                                           int64_t *dev_counts, int64_t capacity,
                                           int64_t *dev_n_distinct);
 
+/* Average cluster sizes of the given species (section "Cluster Analysis"
+ * results: the average cluster size over time; the paper does not name the
+ * average, so both are given).  From the histogram of klmc_cluster_histogram,
+ * with exact int64 sums and one FP64 division each:
+ *   *number_avg = sum s c / sum c        (mean size of a cluster)
+ *   *weight_avg = sum s^2 c / sum s c    (mean size of the cluster holding a
+ *                                         randomly chosen site of the species)
+ * Both are 0 when the species has no site.  Synchronises.  Either output may be
+ * NULL. */
+klmc_status klmc_cluster_averages(klmc_ctx *c, int32_t species, double *number_avg, double *weight_avg);
+
+/* The same two averages of any sparse histogram held in host memory: n pairs
+ * (sizes[k], counts[k]), e.g. one copied back from
+ * klmc_cluster_histogram_device or klmc_batch_cluster_histogram_device.  Host
+ * arithmetic only; no device work.  EINVAL for n < 0, NULL arrays with n > 0, a
+ * negative size or count, or sums beyond int64. */
+klmc_status klmc_histogram_averages(const int64_t *sizes, const int64_t *counts, int64_t n,
+                                    double *number_avg, double *weight_avg);
+
 /* Largest lattice, in sites, accepted by klmc_cluster_histogram_noalloc. */
 #define KLMC_NOALLOC_MAX_SITES (1 << 20)
 

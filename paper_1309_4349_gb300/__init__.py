@@ -108,6 +108,8 @@ def lib():
         "klmc_energy_recount": [vp, P(i64)],
         "klmc_cluster_histogram": [vp, i32, vp, vp, i64, P(i64)],
         "klmc_cluster_histogram_device": [vp, i32, vp, vp, i64, vp],
+        "klmc_cluster_averages": [vp, i32, P(dbl), P(dbl)],
+        "klmc_histogram_averages": [vp, vp, i64, P(dbl), P(dbl)],
         "klmc_get_counters": [vp, P(Counters)],
         "klmc_test_copy_shortfall": [vp, i32],
         "klmc_get_lattice": [vp, vp, i64],
@@ -185,6 +187,19 @@ class _TorchAllocator:
 
         self.alloc = ALLOC_FN(_alloc)
         self.free = FREE_FN(_free)
+
+
+def histogram_averages(sizes, counts) -> tuple[float, float]:
+    """(number average, weight average) of a sparse host histogram
+    (klmc_histogram_averages)."""
+    sz = np.ascontiguousarray(np.asarray(sizes, dtype=np.int64))
+    ct = np.ascontiguousarray(np.asarray(counts, dtype=np.int64))
+    if sz.shape != ct.shape:
+        raise ValueError("sizes and counts differ in length")
+    a, w = ctypes.c_double(), ctypes.c_double()
+    _check(lib().klmc_histogram_averages(sz.ctypes.data, ct.ctypes.data, sz.size, ctypes.byref(a),
+                                         ctypes.byref(w)))
+    return a.value, w.value
 
 
 def make_params(Lx: int, Ly: int | None = None, *, geometry: int = TRI6, packing: int = PACK_BIT,
@@ -285,6 +300,13 @@ class Lattice:
         _check(lib().klmc_cluster_histogram(self._h, int(species), sizes.ctypes.data,
                                             counts.ctypes.data, cap, ctypes.byref(n)))
         return sizes[:n.value].copy(), counts[:n.value].copy()
+
+    def cluster_averages(self, species: int = 1) -> tuple[float, float]:
+        """(number average, weight average) cluster size of the species
+        (klmc_cluster_averages)."""
+        a, w = ctypes.c_double(), ctypes.c_double()
+        _check(lib().klmc_cluster_averages(self._h, int(species), ctypes.byref(a), ctypes.byref(w)))
+        return a.value, w.value
 
     def ffn(self, sample: int = 0) -> tuple[float, float]:
         """(random-neighbour fraction of first neighbours of sample `sample`, all-bond

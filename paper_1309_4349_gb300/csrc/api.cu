@@ -775,6 +775,43 @@ klmc_status klmc_cluster_histogram(klmc_ctx *c, int32_t species, int64_t *sizes,
     return KLMC_OK;
 }
 
+// Average cluster sizes of a sparse histogram: the exact sums n_clusters = sum c,
+// n_sites = sum s c and sum_sq = sum s^2 c in int64 (checked against overflow),
+// then one FP64 division each.
+klmc_status klmc_histogram_averages(const int64_t *sizes, const int64_t *counts, int64_t n,
+                                    double *number_avg, double *weight_avg)
+{
+    if (n < 0 || (n > 0 && (!sizes || !counts))) return fail(KLMC_EINVAL, "bad histogram arrays");
+    long long clusters = 0, sites = 0, sq = 0;
+    for (int64_t k = 0; k < n; ++k) {
+        const long long s = sizes[k], cnt = counts[k];
+        if (s < 0 || cnt < 0) return fail(KLMC_EINVAL, "negative cluster size or count");
+        long long sc = 0, ssc = 0;
+        if (__builtin_mul_overflow(s, cnt, &sc) || __builtin_mul_overflow(sc, s, &ssc) ||
+            __builtin_add_overflow(clusters, cnt, &clusters) || __builtin_add_overflow(sites, sc, &sites) ||
+            __builtin_add_overflow(sq, ssc, &sq))
+            return fail(KLMC_EINVAL, "histogram sums exceed int64");
+    }
+    const double na = clusters > 0 ? (double)sites / (double)clusters : 0.0;
+    const double wa = sites > 0 ? (double)sq / (double)sites : 0.0;
+    if (number_avg) *number_avg = na;
+    if (weight_avg) *weight_avg = wa;
+    return KLMC_OK;
+}
+
+klmc_status klmc_cluster_averages(klmc_ctx *c, int32_t species, double *number_avg, double *weight_avg)
+{
+    if (!c) return fail(KLMC_EINVAL, "ctx is NULL");
+    if (species != 0 && species != 1) return fail(KLMC_EINVAL, "species must be 0 (B) or 1 (A)");
+    klmc_status st = ensure_clusters(c);
+    if (st != KLMC_OK) return st;
+    std::vector<int64_t> sizes((size_t)c->hist_cap), counts((size_t)c->hist_cap);
+    int64_t n = 0;
+    st = klmc_cluster_histogram(c, species, sizes.data(), counts.data(), c->hist_cap, &n);
+    if (st != KLMC_OK) return st;
+    return klmc_histogram_averages(sizes.data(), counts.data(), n, number_avg, weight_avg);
+}
+
 klmc_status klmc_test_copy_shortfall(klmc_ctx *c, int32_t bytes)
 {
     if (!c) return fail(KLMC_EINVAL, "ctx is NULL");

@@ -97,3 +97,34 @@ def test_null_arguments(L):
     assert L.klmc_sweep(None, 1) == 1
     assert L.klmc_energy(None, None, None) == 1
     assert L.klmc_create(None, 64, 0.5, 0.6, 1) == 1
+
+
+def test_histogram_averages_host_arithmetic(L):
+    """klmc_histogram_averages is host arithmetic only: checked here against exact
+    rationals and the oracle's independent implementation, and for its errors."""
+    from fractions import Fraction
+
+    import numpy as np
+
+    import oracle
+
+    cases = [([1, 5], [3, 1]), ([7], [11]), ([], []), ([1, 2, 3, 40], [100, 7, 3, 1]),
+             ([1, (1 << 31) - 1], [1 << 20, 1])]
+    for sizes, counts in cases:
+        got = klmc.histogram_averages(sizes, counts)
+        assert got == oracle.histogram_averages(sizes, counts)
+        c1 = sum(counts)
+        s1 = sum(s * c for s, c in zip(sizes, counts))
+        s2 = sum(s * s * c for s, c in zip(sizes, counts))
+        want = (float(Fraction(s1, c1)) if c1 else 0.0, float(Fraction(s2, s1)) if s1 else 0.0)
+        assert got == want
+    rng = np.random.default_rng(5)
+    for _ in range(20):
+        k = int(rng.integers(1, 30))
+        sizes = np.sort(rng.choice(np.arange(1, 5000), size=k, replace=False))
+        counts = rng.integers(1, 1000, size=k)
+        assert klmc.histogram_averages(sizes, counts) == oracle.histogram_averages(sizes, counts)
+    for sizes, counts in (([1, -2], [1, 1]), ([1], [-1]), ([1 << 32], [1 << 32])):
+        with pytest.raises(klmc.KlmcError) as e:
+            klmc.histogram_averages(sizes, counts)
+        assert e.value.status == 1

@@ -128,5 +128,8 @@ def test_c6_workload_one_run_full():
         sizes, counts = lat.cluster_histogram(1)
         rs, rc = oracle.cluster_histogram(Lx, Ly, oracle.TRI6, t, 1, oracle.HELICAL)
         assert np.array_equal(np.asarray(sizes), rs) and np.array_equal(np.asarray(counts), rc), k
+        # average cluster sizes within 1e-12 relative of the oracle's
+        for got, want in zip(lat.cluster_averages(1), oracle.histogram_averages(rs, rc)):
+            assert abs(got - want) <= 1e-12 * abs(want), k
     assert_same_run(lat, r, Lx, Ly)
     lat.close()

@@ -1,7 +1,9 @@
 """GPU parity: the CUDA library, called through its C ABI, against the CPU oracle.
 
-Every comparison is exact (integer lattice, counters, energies, histograms);
-derived FP64 averages agree to 1e-12 relative.
+Every comparison is exact (integer lattice, counters, energies, histograms).
+The FP64 average cluster sizes (number and weight averages, klmc_cluster_averages)
+are compared with the oracle's within 1e-12 relative (``assert_averages``); both
+sides divide the same exact integer sums, so they agree bit for bit in practice.
 """
 import numpy as np
 import pytest
@@ -24,6 +26,15 @@ PACKS = [klmc.PACK_BIT, klmc.PACK_BYTE]
 def make(Lx, Ly, nA, bw, seed, geometry=klmc.TRI6, packing=klmc.PACK_BIT, cluster=0, threads=0):
     return klmc.Lattice(Lx, Ly, geometry=geometry, packing=packing, n_A=nA, omega_over_kT=bw,
                         seed=seed, cluster=cluster, threads=threads)
+
+
+AVG_RTOL = 1e-12
+
+
+def assert_averages(got, want):
+    """Average cluster sizes within 1e-12 relative (absolute 0 for an empty species)."""
+    for g, w in zip(got, want):
+        assert abs(g - w) <= AVG_RTOL * abs(w), (got, want)
 
 
 def assert_same_run(lat, ref):
@@ -301,6 +312,7 @@ def _hist_equal(lat, t, species):
     rs, rc = oracle.cluster_histogram(lat.Lx, lat.Ly, lat.geometry, t, species)
     assert np.array_equal(s, rs) and np.array_equal(c, rc)
     assert int((s * c).sum()) == int((t == species).sum())
+    assert_averages(lat.cluster_averages(species), oracle.histogram_averages(rs, rc))
 
 
 @pytest.mark.parametrize("geometry", GEOMS)
@@ -394,6 +406,8 @@ def test_batch_histograms_match_oracle():
             assert k == rs.size and k <= cap
             assert np.array_equal(sizes[i, :k].cpu().numpy(), rs)
             assert np.array_equal(counts[i, :k].cpu().numpy(), rc)
+            assert_averages(klmc.histogram_averages(sizes[i, :k].cpu().numpy(), counts[i, :k].cpu().numpy()),
+                            oracle.histogram_averages(rs, rc))
     small = torch.zeros((n, 1), dtype=torch.int64, device="cuda")
     nd = torch.zeros((n,), dtype=torch.int64, device="cuda")
     b.cluster_histogram_device(1, small, small.clone(), nd)
@@ -546,5 +560,9 @@ def test_c1_workload_full():
         sizes, counts = lat.cluster_histogram(1)
         rs, rc = oracle.cluster_histogram(L, L, klmc.TRI6, t, 1)
         assert np.array_equal(np.asarray(sizes), rs) and np.array_equal(np.asarray(counts), rc), k
+        want = oracle.histogram_averages(rs, rc)
+        assert_averages(lat.cluster_averages(1), want)
+        assert_averages(klmc.histogram_averages(sizes, counts), want)
+        assert_averages(lat.cluster_averages(0), oracle.cluster_averages(L, L, klmc.TRI6, t, 0))
     assert_same_run(lat, r)
     lat.close()
