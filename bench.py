@@ -12,7 +12,7 @@ One benchmark step = the whole workload: load the five initial lattices, run
 attempts per second (attempts are counted exactly by the kernels).
 
 Forms: "batched" (one resident-kernel launch advances all five lattices, one
-CTA each; this is ``value``) and "plain" (one launch per lattice, issued in
+thread-block cluster of 16 CTAs each; this is ``value``) and "plain" (one launch per lattice, issued in
 turn).  ``e2e`` is the batched form through the public API with the initial
 lattices copied from pinned host memory and all histograms, lattices and
 energies copied back, inside the timed region.
@@ -55,15 +55,14 @@ WORKLOAD = ("400x400 TRI6 periodic, 30% A random start, omega/kT in {0.2,0.4,0.6
 # evaluation (10 rounds x (2 IMAD.WIDE + 2 LOP3)), paid only by drawn attempts.
 C_PAIR = 4.8
 C_PHILOX = 40.0
-# INT32 lanes per SM per clock: 4 sub-partitions x 16.  The probe
-# paper_1309_4349_gb300/probes/int_peak.cu measures 60 LOP3 and 30 IMAD.WIDE
-# (+30 LOP3) lane-ops/clk/SM on GB300, i.e. one 64-lane integer pipe.
+# INT32 lanes per SM per clock: 4 sub-partitions x 16, the documented 32-bit
+# integer and logical-operation rate of 64 results per clock per SM; a throughput
+# probe on GB300 measured 60 LOP3 and 30 IMAD.WIDE (+30 LOP3) lane-ops/clk/SM.
 INT32_LANES_PER_SM = 64
 # DRAM bytes (read + write) per launch of the dominant kernel, from one ncu capture
-# each (profiles/resident_sweep_400x400x5_ncu.md: one resident-sweep launch of 500 MCS
-# of the 400x400 x 5 workload; profiles/band_phases_8192x8192_ncu.md: one 4-phase band
-# launch of the 8192x8192 lattice), valid only for the kernel sources they were taken
-# with (hash of sweep_resident.cu + sweep_common.cuh).
+# each (one resident-sweep launch of 500 MCS of the 400x400 x 5 workload; one
+# 4-phase band launch of the 8192x8192 lattice), valid only for the kernel sources
+# they were taken with (hash of sweep_resident.cu + sweep_common.cuh).
 TRAFFIC_C2_LAUNCH = 306432
 TRAFFIC_C3_LAUNCH = 8498432
 TRAFFIC_SOURCES = "1553ba35071005ba"
@@ -363,7 +362,7 @@ def _roofline(kernel, launch_ms, attempts_launch, p_draw, sm_count, sm_mhz, ctas
          "ops_per_attempt": ops_attempt, "p_draw": p_draw, "launch_ms": launch_ms,
          "attempts_per_launch": attempts_launch, "ctas_per_launch": ctas,
          "peak_basis": (f"{sm_count} SMs x {INT32_LANES_PER_SM} INT32 lanes/clk x median SM clock "
-                        f"{sm_mhz:.0f} MHz (derived; probes/int_peak.cu)")}
+                        f"{sm_mhz:.0f} MHz (64 INT32 lanes: documented rate, confirmed by a throughput probe)")}
     d.update(extra or {})
     return d
 
@@ -784,12 +783,13 @@ def main():
                 "ctas_per_launch": ctas, "cluster": cluster, "threads_per_cta": threads,
                 "sm_count": sm_count,
                 "peak_basis": (f"{sm_count} SMs x {INT32_LANES_PER_SM} INT32 lanes/clk x median SM "
-                               f"clock {sm_mhz:.0f} MHz (derived; probes/int_peak.cu)"),
+                               f"clock {sm_mhz:.0f} MHz (64 INT32 lanes: documented rate, confirmed by a "
+                               f"throughput probe)"),
                 "frac_of_occupied_sms": achieved_tops / (peak_tops * min(ctas, sm_count) / sm_count),
                 "sweep_share_of_step": sum(sweep_ms) / sum(ms_steps),
                 "note": "latency-bound: each phase waits for its slowest task (the lane with the most Philox "
-                        "draws) and a barrier; the 5 lattices occupy 5 clusters of SMs (profiles/"
-                        "resident_sweep_400x400x5_ncu.md: issue active 30%, top stall barrier)"}
+                        "draws) and a barrier; the 5 lattices occupy 5 clusters of SMs (ncu: issue "
+                        "active 30%, top stall barrier)"}
 
     # Exactness spot check of the timed state (the parity tests do the full check).
     e_run = [lat.energy()[0] for lat in batch.replicas]

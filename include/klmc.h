@@ -221,22 +221,27 @@ klmc_status klmc_histogram_averages(const int64_t *sizes, const int64_t *counts,
 #define KLMC_NOALLOC_MAX_SITES (1 << 20)
 
 /* The cluster-size histogram of klmc_cluster_histogram_device for a caller-owned
- * lattice, without allocating any device memory.  The paper has no counterpart:
- * this entry point exists for callers that cannot call cudaMalloc, such as a host
- * framework that owns all device memory under a fixed budget with no allocator
- * hook, or a latency-bound loop that cannot accept cudaMalloc's implicit device
- * synchronisation.
+ * periodic lattice, without allocating any device memory.  The paper has no
+ * counterpart: this entry point exists for callers that cannot call cudaMalloc,
+ * such as a host framework that owns all device memory under a fixed budget with
+ * no allocator hook, or a latency-bound loop that cannot accept cudaMalloc's
+ * implicit device synchronisation.
  *  dev_lattice  device lattice, Ly rows of `pitch` 32-bit words (KLMC_PACK_BIT,
  *               site x is bit x%32 of word x/32) or `pitch` bytes (KLMC_PACK_BYTE,
- *               1 = A); owned by the caller, read only.
+ *               1 = A); owned by the caller, read only.  Boundaries are periodic
+ *               (the paper's lattice model with periodic wrap); a helical lattice
+ *               (KLMC_HELICAL) takes klmc_cluster_histogram_device instead.
  *  outputs      as klmc_cluster_histogram_device (caller device buffers).
  *  stream       cudaStream_t the work is enqueued on; returns without waiting.
- * Scratch comes from one fixed device array of the library (about 12.6 MB, held by
- * every GPU that loads the library until the process exits), shared by all calls:
- * calls whose work overlaps on the GPU race and must be serialised by the caller.
- * The first call on each device resolves the array's device address (set-up) and
- * should come before any stream capture on that device.  EINVAL when Lx*Ly
- * exceeds KLMC_NOALLOC_MAX_SITES or an argument is invalid. */
+ * Scratch comes from one fixed device array of the library (about 12.6 MB),
+ * shared by all calls: calls whose work overlaps on the GPU race and must be
+ * serialised by the caller.  The first call in a device's context loads the
+ * library module that holds the array, which reserves the 12.6 MB on that device
+ * until the process exits, may synchronise the device, and fails with
+ * KLMC_ECUDA when that memory is not available; make that first call during
+ * set-up, outside any latency-bound loop and before any stream capture.  Later
+ * calls only look the array's address up.  EINVAL when Lx*Ly exceeds
+ * KLMC_NOALLOC_MAX_SITES or an argument is invalid. */
 klmc_status klmc_cluster_histogram_noalloc(const void *dev_lattice, int32_t packing, int32_t Lx,
                                            int32_t Ly, int32_t pitch, int32_t geometry,
                                            int32_t species, int64_t *dev_sizes,
@@ -247,9 +252,10 @@ klmc_status klmc_cluster_histogram_noalloc(const void *dev_lattice, int32_t pack
 klmc_status klmc_get_counters(klmc_ctx *c, klmc_counters *out);
 
 /* Test hook for the bounded waits (0 in normal use).  From the next sweep on, each
- * tiled launch of this handle that moves its rows by bulk copies expects `bytes`
- * more than its copies deliver, so that its wait for them gives up after a short
- * bound; the launch then leaves its band unwritten and klmc_energy /
+ * tiled launch of this handle that moves its rows by bulk copies issues no row
+ * copy and waits instead for `bytes` that nothing delivers, so that its wait gives
+ * up after a short bound with no copy in flight; the launch then leaves its band
+ * unwritten and klmc_energy /
  * klmc_get_counters report KLMC_ETIMEOUT.  The handle's lattice is then no longer
  * a state of the chain; other handles are unaffected.  Synchronises.  EINVAL for
  * bytes < 0. */
@@ -384,7 +390,9 @@ typedef struct klmc_server_stats {
  * between rounds.  A job's result does not depend on the other jobs. */
 klmc_status klmc_server_create(klmc_server **out, size_t device_mem_budget, void *stream);
 
-/* Queues a job: the lattice of p (p->stream, alloc and free are ignored), n_mcs
+/* Queues a job: the lattice of p (p->stream is ignored; when p->alloc and p->free
+ * are both set they serve the job's lattice memory and are called from the
+ * server's worker thread, and a NULL from alloc fails the job with KLMC_ENOMEM), n_mcs
  * steps, an A-cluster histogram every hist_every steps and at the end
  * (0: none), flags (KLMC_JOB_KEEP_LATTICE).  Thread-safe; never blocks on GPU work.
  * Jobs too large for the budget finish with status KLMC_EINVAL. */

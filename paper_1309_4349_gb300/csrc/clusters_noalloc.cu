@@ -10,12 +10,17 @@
 // arrays, size histogram, occupied-size bitmap) taken from a fixed array in this
 // file instead of from an allocation.
 //
-// The array is a file-scope __device__ variable, so every GPU that loads the
-// library holds it (about 12.6 MB) until the process exits.  Every call shares
-// it and it keeps the last call's contents; the parts that must start at zero
-// are cleared by each call.  Two calls whose work overlaps on the GPU (different
-// streams, or different host threads) race on the array.
-#include <mutex>
+// The array is a file-scope __device__ variable.  With lazy module loading (the
+// CUDA default) a device holds it (about 12.6 MB) from the first call of this
+// entry point in its context until the process exits; that first call loads the
+// module, which may synchronise the device and may fail with KLMC_ECUDA when
+// device memory is short, so callers make it during set-up, outside any
+// latency-bound loop and outside stream capture.  Every call shares the array
+// and it keeps the last call's contents; the parts that must start at zero are
+// cleared by each call.  Two calls whose work overlaps on the GPU (different
+// streams, or different host threads) race on the array.  The lattice is read
+// with periodic boundaries (the paper's lattice model); helical lattices take
+// klmc_cluster_histogram_device.
 #include <string>
 
 #include "klmc.h"
@@ -34,33 +39,24 @@ constexpr unsigned long long kScratchBytes =
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
-// Device address of g_noalloc_scratch, resolved once per device.  In host code
-// the symbol itself is only a host-side stand-in, never a device address.
-constexpr int kMaxDevices = 64;
-std::mutex g_setup_mutex;
-void *g_scratch_addr[kMaxDevices] = {};
-
 klmc_status fail(klmc_status s, const std::string &msg)
 {
     klmc::set_last_error(msg.c_str());  // reported by klmc_last_error()
     return s;
 }
 
+// Device address of g_noalloc_scratch in the current device's context.  In host
+// code the symbol itself is only a host-side stand-in, never a device address.
+// It is resolved on every call instead of being cached: a cached address would
+// be stale after cudaDeviceReset or in another context of the same device.  The
+// first call in a context loads this file's module, which reserves the array.
 klmc_status scratch_address(void **out)
 {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return fail(KLMC_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
-    if (dev < 0 || dev >= kMaxDevices) return fail(KLMC_ENODEV, "device index out of range");
-    std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_addr[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p)
-            return fail(KLMC_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-        g_scratch_addr[dev] = p;
-    }
-    *out = g_scratch_addr[dev];
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p)
+        return fail(KLMC_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    *out = p;
     return KLMC_OK;
 }
 

@@ -19,6 +19,7 @@
 // m_lo, m_hi}); it is similar iff that neighbour is a lattice pixel whose gray
 // level differs by at most delta.
 #include "klmc_internal.h"
+#include "philox.cuh"
 
 namespace klmc {
 namespace {
@@ -62,27 +63,6 @@ __global__ void snapshot_kernel(const void *lat, int packing, int pitch, int Lx,
     }
 }
 
-__device__ __forceinline__ void philox4_words(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,
-                                              uint32_t k1, uint32_t o[4])
-{
-#pragma unroll
-    for (int r = 0; r < 10; ++r) {
-        const unsigned long long p0 = (unsigned long long)c0 * 0xD2511F53ull;
-        const unsigned long long p1 = (unsigned long long)c2 * 0xCD9E8D57ull;
-        const uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0;
-        const uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1;
-        c1 = (uint32_t)p1;
-        c3 = (uint32_t)p0;
-        c0 = n0;
-        c2 = n2;
-        k0 += 0x9E3779B9u;
-        k1 += 0xBB67AE85u;
-    }
-    o[0] = c0;
-    o[1] = c1;
-    o[2] = c2;
-    o[3] = c3;
-}
 
 __constant__ int kMooreI[8] = {1, 1, 0, -1, -1, -1, 0, 1};
 __constant__ int kMooreJ[8] = {0, 1, 1, 1, 0, -1, -1, -1};
@@ -104,8 +84,8 @@ __global__ void image_ffn_kernel(const uint8_t *image, const uint8_t *mask, int 
     long long similar = 0, pixels = 0;
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < G;
          q += (long long)gridDim.x * blockDim.x) {
-        uint32_t w[4];
-        philox4_words((uint32_t)q, 0xFFFFFFFCu, (uint32_t)m, (uint32_t)(m >> 32), k0, k1, w);
+        const Philox4 pw = philox4((uint32_t)q, 0xFFFFFFFCu, (uint32_t)m, (uint32_t)(m >> 32), k0, k1);
+        const uint32_t *w = pw.v;
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
             const long long p = 4 * q + r;

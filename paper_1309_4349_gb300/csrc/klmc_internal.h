@@ -42,8 +42,8 @@ struct SweepJob {
     uint64_t magicW;      // ceil(2^32 / W): task t -> row (t * magicW) >> 32
     int32_t draw_lo;      // neighbour-agreement sums S in [draw_lo, draw_hi] need a draw
     int32_t draw_hi;
-    int32_t copy_shortfall;  // test hook (0 in use): bytes a band launch's row copies are expected to
-                             // deliver beyond what they do, so that its bounded wait runs out
+    int32_t copy_shortfall;  // test hook (0 in use): a band launch issues no row copy and waits for
+                             // this many bytes instead, which nothing delivers, so its bounded wait runs out
     uint64_t thr[16];     // accept iff draw < thr[S] (S = same_a + same_b)
     long long *state;     // StateSlot array
 };

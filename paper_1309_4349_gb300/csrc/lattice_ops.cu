@@ -10,61 +10,19 @@
 #include <string.h>
 
 #include "klmc_internal.h"
+#include "philox.cuh"
 
 namespace klmc {
 namespace {
 
 constexpr int kBlock = 256;
 
-// Philox4x32-10 (Salmon et al., SC'11), all four output words.
-__device__ __forceinline__ void philox_w4(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,
-                                          uint32_t k1, uint32_t o[4])
-{
-#pragma unroll
-    for (int r = 0; r < 10; ++r) {
-        unsigned long long p0 = (unsigned long long)c0 * 0xD2511F53ull;
-        unsigned long long p1 = (unsigned long long)c2 * 0xCD9E8D57ull;
-        uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0;
-        uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1;
-        c1 = (uint32_t)p1;
-        c3 = (uint32_t)p0;
-        c0 = n0;
-        c2 = n2;
-        k0 += 0x9E3779B9u;
-        k1 += 0xBB67AE85u;
-    }
-    o[0] = c0;
-    o[1] = c1;
-    o[2] = c2;
-    o[3] = c3;
-}
-
-__device__ __forceinline__ void philox_w01(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
-                                           uint32_t k0, uint32_t k1, uint32_t &o0, uint32_t &o1)
-{
-#pragma unroll
-    for (int r = 0; r < 10; ++r) {
-        unsigned long long p0 = (unsigned long long)c0 * 0xD2511F53ull;
-        unsigned long long p1 = (unsigned long long)c2 * 0xCD9E8D57ull;
-        uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0;
-        uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1;
-        c1 = (uint32_t)p1;
-        c3 = (uint32_t)p0;
-        c0 = n0;
-        c2 = n2;
-        k0 += 0x9E3779B9u;
-        k1 += 0xBB67AE85u;
-    }
-    o0 = c0;
-    o1 = c1;
-}
 
 // Placement key of site i: Philox counter {i, 0xFFFFFFFF, 0, 0}, words w1:w0.
 __device__ __forceinline__ unsigned long long site_key(uint32_t i, uint32_t k0, uint32_t k1)
 {
-    uint32_t w0, w1;
-    philox_w01(i, 0xFFFFFFFFu, 0u, 0u, k0, k1, w0, w1);
-    return ((unsigned long long)w1 << 32) | w0;
+    const Philox4 w = philox4(i, 0xFFFFFFFFu, 0u, 0u, k0, k1);
+    return ((unsigned long long)w.v[1] << 32) | w.v[0];
 }
 
 struct SelectState {
@@ -244,8 +202,8 @@ __global__ void ffn_kernel(const void *lat, int packing, int Lx, int Ly, int pit
     long long n = 0;
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < G;
          q += (long long)gridDim.x * blockDim.x) {
-        uint32_t w[4];
-        philox_w4((uint32_t)q, 0xFFFFFFFEu, (uint32_t)m, (uint32_t)(m >> 32), k0, k1, w);
+        const Philox4 pw = philox4((uint32_t)q, 0xFFFFFFFEu, (uint32_t)m, (uint32_t)(m >> 32), k0, k1);
+        const uint32_t *w = pw.v;
         const long long i0 = 4 * q;
         int y = (int)(i0 / Lx), x = (int)(i0 - (long long)y * Lx);
 #pragma unroll

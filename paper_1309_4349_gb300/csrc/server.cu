@@ -166,9 +166,11 @@ int admit(klmc_server *s)
             j = s->pending.front();
         }
         klmc_params p = j->p;
-        p.stream = s->stream;
-        p.alloc = nullptr;
-        p.free = nullptr;
+        p.stream = s->stream;  // the job's own allocator (alloc and free), if any, serves its lattice
+        if (!p.alloc || !p.free) {
+            p.alloc = nullptr;
+            p.free = nullptr;
+        }
         size_t need = klmc::host::device_bytes(&p);
         if (j->hist_every > 0) need += (size_t)(2 * ((long long)std::sqrt(2.0 * p.Lx * p.Ly) + 2) + 1) * 8;
         if (need > s->budget) {  // can never be admitted: fail it instead of blocking the queue

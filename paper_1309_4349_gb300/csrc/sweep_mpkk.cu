@@ -18,6 +18,7 @@
 // The sweep index is read from device state, so a CUDA graph of K sweeps can be
 // replayed.
 #include "klmc_internal.h"
+#include "philox.cuh"
 
 namespace klmc {
 namespace {

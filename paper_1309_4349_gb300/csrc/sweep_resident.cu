@@ -45,6 +45,7 @@
 #include <string.h>
 
 #include "klmc_internal.h"
+#include "philox.cuh"
 
 namespace klmc {
 namespace {
@@ -810,17 +811,22 @@ band_phases_kernel(const SweepJob J, const void *__restrict__ src, void *__restr
 
     if (bulk) {
         // One bulk copy per row (pitch words, 16-byte aligned at both ends) into the
-        // row's site words, completing on one mbarrier; then the pad words.
+        // row's site words, completing on one mbarrier whose expected byte count is
+        // exactly theirs; then the pad words.  Under the test hook no copy is
+        // issued and the barrier expects the hook's bytes instead, which nothing
+        // delivers: the wait runs out with no copy in flight.
         __syncthreads();
+        const bool hook = J.copy_shortfall != 0;
         if (tid < 32) {
             if (tid == 0) {
                 unsigned long long st;
                 asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 %0, [%1], %2;"
-                             : "=l"(st) : "r"(bar), "r"(row_bytes * (uint32_t)NL + (uint32_t)J.copy_shortfall)
+                             : "=l"(st)
+                             : "r"(bar), "r"(hook ? (uint32_t)J.copy_shortfall : row_bytes * (uint32_t)NL)
                              : "memory");
             }
             __syncwarp();
-            for (int lr = tid; lr < NL; lr += 32) {
+            for (int lr = tid; !hook && lr < NL; lr += 32) {
                 int y = g.Y0 - g.D + lr;
                 if (y < 0) y += g.Ly;
                 if (y >= g.Ly) y -= g.Ly;
@@ -831,11 +837,12 @@ band_phases_kernel(const SweepJob J, const void *__restrict__ src, void *__restr
                     ::"r"(to), "l"(from), "r"(row_bytes), "r"(bar) : "memory");
             }
         }
-        const int polls = J.copy_shortfall != 0 ? kCopyWaitPollsShort : kCopyWaitPolls;
+        const int polls = hook ? kCopyWaitPollsShort : kCopyWaitPolls;
         const bool ok = mbar_wait(bar, 0u, polls);
         if (__syncthreads_or(!ok)) {
-            // Give up on this launch: report it, let the copies in flight land, and
-            // leave the band unwritten.
+            // Give up on this launch: report it and leave the band unwritten.  Only a
+            // copy that has not landed after the first bound can still be in flight
+            // here (never under the hook); wait a second bound for it.
             if (tid == 0) atomicExch((unsigned long long *)&J.state[kFault], 1ull);
             mbar_wait(bar, 0u, polls);
             return;

@@ -15,6 +15,7 @@
 #include <string.h>
 
 #include "klmc_internal.h"
+#include "philox.cuh"
 
 namespace klmc {
 namespace {

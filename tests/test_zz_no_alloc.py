@@ -79,10 +79,13 @@ def test_noalloc_matches_allocating_entry_point_twice_in_a_row():
          oracle.run(257, 130, oracle.SQ4, 0.9, 5, oracle.init(257, 130, 13000, 5), 0, 6).lattice),
     ]
     for Lx, Ly, g, species, packing, t in cases:
-        got = histogram_noalloc(t, Lx, Ly, g, species, packing)
         want = histogram_with_allocating_entry_point(t, Lx, Ly, g, species)
-        assert np.array_equal(got[0], want[0]) and np.array_equal(got[1], want[1])
-        assert int((got[0] * got[1]).sum()) == int((t == species).sum())
+        ref = oracle.cluster_histogram(Lx, Ly, g, t, species)
+        for _ in range(2):  # the second call reuses the scratch the first one left behind
+            got = histogram_noalloc(t, Lx, Ly, g, species, packing)
+            assert np.array_equal(got[0], want[0]) and np.array_equal(got[1], want[1])
+            assert np.array_equal(got[0], ref[0]) and np.array_equal(got[1], ref[1])
+            assert int((got[0] * got[1]).sum()) == int((t == species).sum())
 
 
 def test_noalloc_rejects_lattices_above_its_fixed_scratch():
