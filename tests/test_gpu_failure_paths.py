@@ -24,8 +24,8 @@ ENOMEM = 2
 
 class FailingAllocator:
     """Device allocator backed by torch's caching allocator that returns NULL on
-    its allocation number `fail_at` (0-based; None: never) and on every later one
-    while `refuse` is set.  `outstanding` holds the pointers not yet freed."""
+    its allocation number `fail_at` (0-based; None: never), and on every one while
+    `refuse` is set.  `outstanding` holds the pointers not yet freed."""
 
     def __init__(self, fail_at=None):
         self.fail_at = fail_at
@@ -37,7 +37,7 @@ class FailingAllocator:
         def _alloc(nbytes, stream, user):
             k = self.calls
             self.calls += 1
-            if self.refuse or (self.fail_at is not None and k >= self.fail_at):
+            if self.refuse or k == self.fail_at:
                 return None
             ptr = int(torch.cuda.caching_allocator_alloc(int(nbytes), device=dev, stream=stream or 0))
             self.outstanding[ptr] = int(nbytes)
