@@ -566,3 +566,76 @@ def test_c1_workload_full():
         assert_averages(lat.cluster_averages(0), oracle.cluster_averages(L, L, klmc.TRI6, t, 0))
     assert_same_run(lat, r)
     lat.close()
+
+
+def test_8192_full_size_graph_block_against_oracle():
+    """The 8192 x 8192, 1 bit per site, omega/kT = 0.85 lattice as the benchmark runs
+    it: one traced graph replay of 10 sweeps (20 band launches of 4 phases, the
+    energy trace every 10 MCS) against the oracle, lattice, counters, energy and
+    trace; then two more replays against the oracle continued from that state."""
+    L = 8192
+    nA = L * L // 2
+    lat = make(L, L, nA, 0.85, 7)
+    assert lat.launch_shape()[0] == -1
+    t0 = oracle.init(L, L, nA, 7)
+    tr = lat.sweep_traced(10, 10)
+    ref = oracle.run(L, L, klmc.TRI6, 0.85, 7, t0, 0, 10, trace_every=10)
+    assert_same_run(lat, ref)
+    assert tr.cpu().numpy().tolist() == ref.trace.tolist()
+    lat.sweep(16)  # two replays of the untraced 8-sweep graph
+    ref2 = oracle.run(L, L, klmc.TRI6, 0.85, 7, ref.lattice, 10, 16, n_unlike0=ref.n_unlike,
+                      counters0=ref.counters())
+    assert_same_run(lat, ref2)
+    lat.close()
+
+
+def test_c4_all_replicas_against_oracle():
+    """All 256 replicas of the batched workload as the benchmark builds them, in one
+    batch at the shapes the batch chooses, for 5 MCS: every replica's lattice,
+    counters and energy equal its own oracle run (the oracle spread over host
+    threads)."""
+    import concurrent.futures
+
+    import bench
+
+    reps = bench.c4_replicas()
+    b = klmc.Batch(reps)
+    n = 5
+    b.sweep([n] * len(reps))
+
+    def ref_of(r):
+        nA = oracle.n_A(r["Lx"], r["Ly"], -1, r["fraction_A"])
+        return oracle.run(r["Lx"], r["Ly"], klmc.TRI6, r["omega_over_kT"], r["seed"],
+                          oracle.init(r["Lx"], r["Ly"], nA, r["seed"]), 0, n)
+
+    with concurrent.futures.ThreadPoolExecutor(max_workers=16) as ex:
+        refs = list(ex.map(ref_of, reps))
+    shapes = set()
+    for i, ref in enumerate(refs):
+        assert_same_run(b.replicas[i], ref)
+        shapes.add(b.launch_shape(i))
+    assert len(shapes) >= 2  # the batch ran several launch shapes
+    b.close()
+
+
+def test_c2_one_run_2000_mcs_all_histograms():
+    """One of the 400 x 400 workload's runs (omega/kT 0.6, its seed) for 2000 MCS
+    with the histogram cadence of 500 MCS: all four histograms, their averages, and
+    the final lattice, counters and energy equal the oracle's."""
+    import bench
+
+    Lx = Ly = bench.L
+    w, seed = bench.OMEGAS[2], bench.SEEDS[2]
+    nA = oracle.n_A(Lx, Ly, -1, bench.FRACTION_A)
+    lat = klmc.Lattice(Lx, Ly, fraction_A=bench.FRACTION_A, omega_over_kT=w, seed=seed)
+    t = oracle.init(Lx, Ly, nA, seed)
+    assert np.array_equal(lat.get_lattice(), t)
+    nu, cnt = None, (0, 0, 0, 0)
+    for k in range(4):
+        lat.sweep(bench.HIST_EVERY)
+        r = oracle.run(Lx, Ly, klmc.TRI6, w, seed, t, k * bench.HIST_EVERY, bench.HIST_EVERY,
+                       n_unlike0=nu, counters0=cnt)
+        t, nu, cnt = r.lattice, r.n_unlike, r.counters()
+        _hist_equal(lat, t, 1)
+    assert_same_run(lat, r)
+    lat.close()
