@@ -70,6 +70,7 @@ def test_create_enomem_at_every_allocation():
         st, h = create(fa)
         if st == 0:
             n_allocs = k
+            fa.fail_at = None  # allocations on first use (the byte lattice) are granted
             lat = klmc.Lattice(0, _handle=h)
             lat.sweep(3)
             ref = oracle.run(64, 48, klmc.TRI6, 0.7, 11, oracle.init(64, 48, 64 * 48 // 3, 11), 0, 3)
