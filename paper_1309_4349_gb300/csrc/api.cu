@@ -257,6 +257,10 @@ klmc_status create_one(klmc_ctx **out, const klmc_params *p, klmc_batch *owner, 
     J.magicW = (0x100000000ull + (unsigned long long)c->W - 1) / (unsigned long long)c->W;
     J.key0 = (uint32_t)p->seed;
     J.key1 = (uint32_t)(p->seed >> 32);
+    for (int r = 2; r < 10; ++r) {  // Philox4x32-10 round keys (Weyl sequence of the key)
+        J.rk[0][r - 2] = J.key0 + (uint32_t)r * 0x9E3779B9u;
+        J.rk[1][r - 2] = J.key1 + (uint32_t)r * 0xBB67AE85u;
+    }
     J.state = c->state;
     st = build_thresholds(p->omega_over_kT, p->geometry, &J);
     if (st != KLMC_OK) {

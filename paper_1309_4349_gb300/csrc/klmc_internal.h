@@ -46,6 +46,7 @@ struct SweepJob {
                              // this many bytes instead, which nothing delivers, so its bounded wait runs out
     uint64_t thr[16];     // accept iff draw < thr[S] (S = same_a + same_b)
     long long *state;     // StateSlot array
+    uint32_t rk[2][8];    // Philox round keys of rounds 2..9: key0 + r W0, key1 + r W1
 };
 
 // Per-call arguments of one lattice.

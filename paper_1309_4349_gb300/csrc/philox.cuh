@@ -112,6 +112,47 @@ __device__ __forceinline__ void philox2_w0_key(uint32_t a0, uint32_t b0, const D
     rb = xb0;
 }
 
+// philox2_w0_key with the keys of rounds 2..9 read from rk (rk[0][r-2] = k0 + r W0,
+// rk[1][r-2] = k1 + r W1), for callers that keep them in the kernel's parameter
+// space, where an operand costs no instruction.
+__device__ __forceinline__ void philox2_w0_rk(uint32_t a0, uint32_t b0, const DrawKey &d, const uint32_t (&rk)[2][8],
+                                              uint32_t &ra, uint32_t &rb)
+{
+    const unsigned long long qa = (unsigned long long)a0 * kPhiloxM0;
+    const unsigned long long qb = (unsigned long long)b0 * kPhiloxM0;
+    const uint32_t a2r = (uint32_t)(qa >> 32) ^ d.sk, b2r = (uint32_t)(qb >> 32) ^ d.sk;
+    const unsigned long long ta = (unsigned long long)a2r * kPhiloxM1;
+    const unsigned long long tb = (unsigned long long)b2r * kPhiloxM1;
+    uint32_t xa0 = (uint32_t)(ta >> 32) ^ d.bk, xa1 = (uint32_t)ta, xa2 = d.hk ^ (uint32_t)qa, xa3 = d.la;
+    uint32_t xb0 = (uint32_t)(tb >> 32) ^ d.bk, xb1 = (uint32_t)tb, xb2 = d.hk ^ (uint32_t)qb, xb3 = d.la;
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+        const unsigned long long pa0 = (unsigned long long)xa0 * kPhiloxM0;
+        const unsigned long long pa1 = (unsigned long long)xa2 * kPhiloxM1;
+        const unsigned long long pb0 = (unsigned long long)xb0 * kPhiloxM0;
+        const unsigned long long pb1 = (unsigned long long)xb2 * kPhiloxM1;
+        const uint32_t na0 = (uint32_t)(pa1 >> 32) ^ xa1 ^ rk[0][r];
+        const uint32_t na2 = (uint32_t)(pa0 >> 32) ^ xa3 ^ rk[1][r];
+        const uint32_t nb0 = (uint32_t)(pb1 >> 32) ^ xb1 ^ rk[0][r];
+        const uint32_t nb2 = (uint32_t)(pb0 >> 32) ^ xb3 ^ rk[1][r];
+        xa1 = (uint32_t)pa1; xa3 = (uint32_t)pa0; xa0 = na0; xa2 = na2;
+        xb1 = (uint32_t)pb1; xb3 = (uint32_t)pb0; xb0 = nb0; xb2 = nb2;
+    }
+    ra = xa0;
+    rb = xb0;
+}
+
+__device__ __forceinline__ uint32_t philox_w0_rk(uint32_t a0, const DrawKey &d, const uint32_t (&rk)[2][8])
+{
+    const unsigned long long qa = (unsigned long long)a0 * kPhiloxM0;
+    const uint32_t a2r = (uint32_t)(qa >> 32) ^ d.sk;
+    const unsigned long long ta = (unsigned long long)a2r * kPhiloxM1;
+    uint32_t x0 = (uint32_t)(ta >> 32) ^ d.bk, x1 = (uint32_t)ta, x2 = d.hk ^ (uint32_t)qa, x3 = d.la;
+#pragma unroll
+    for (int r = 0; r < 8; ++r) philox_round(x0, x1, x2, x3, rk[0][r], rk[1][r]);
+    return x0;
+}
+
 // Word 0 of one counter {a0, f, s_lo, s_hi} with the phase's DrawKey.
 __device__ __forceinline__ uint32_t philox_w0_key(uint32_t a0, const DrawKey &d)
 {

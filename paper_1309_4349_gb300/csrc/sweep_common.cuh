@@ -308,10 +308,12 @@ __device__ __forceinline__ uint32_t draw_accepts(uint32_t dmask, const Planes &S
 constexpr int kDrawQueue2 = 512;
 constexpr int kDrawQueue2Words = 2 * 32 * 4 + 2 * 32 + 2 * 32 + kDrawQueue2 / 2;
 
+template <bool RK>  // RK: the round keys from rk (kernel parameter space); else from dk
 __device__ __forceinline__ void draw_accepts_queue2(uint32_t dmask0, const Planes &S0, uint32_t base0,
                                                     uint32_t dmask1, const Planes &S1, uint32_t base1,
-                                                    const DrawKey &dk, const uint64_t *thr, uint32_t *q,
-                                                    uint32_t &acc0, uint32_t &acc1)
+                                                    const DrawKey &dk, const uint32_t (&rk)[2][8],
+                                                    const uint64_t *thr, uint32_t *q, uint32_t &acc0,
+                                                    uint32_t &acc1)
 {
     acc0 = 0u;
     acc1 = 0u;
@@ -356,20 +358,34 @@ __device__ __forceinline__ void draw_accepts_queue2(uint32_t dmask0, const Plane
         ent[slot++] = (uint16_t)(1024u | ((uint32_t)lane << 5) | (uint32_t)p);
     }
     __syncwarp();
-    for (int k = lane; k < total; k += 64) {
-        const uint32_t e1 = ent[k];
-        const bool two = k + 32 < total;
-        const uint32_t e2 = two ? ent[k + 32] : e1;
-        const uint32_t r1i = e1 >> 5, p1 = e1 & 31u, r2i = e2 >> 5, p2 = e2 & 31u;  // record = task*32 + lane
-        uint32_t r1, r2;
-        philox2_w0_key(sites[r1i] + p1, sites[r2i] + p2, dk, r1, r2);
-        const uint4 a = planes[r1i], b = planes[r2i];
-        const uint32_t Sa = ((a.x >> p1) & 1u) | (((a.y >> p1) & 1u) << 1) | (((a.z >> p1) & 1u) << 2) |
-                            (((a.w >> p1) & 1u) << 3);
-        const uint32_t Sb = ((b.x >> p2) & 1u) | (((b.y >> p2) & 1u) << 1) | (((b.z >> p2) & 1u) << 2) |
-                            (((b.w >> p2) & 1u) << 3);
-        if ((uint64_t)r1 < thr[Sa]) atomicOr(wacc + r1i, 1u << p1);
-        if (two && (uint64_t)r2 < thr[Sb]) atomicOr(wacc + r2i, 1u << p2);
+    // Rounds of 64 entries, lane i taking entries i and i + 32 (two Philox chains);
+    // a last round of at most 32 entries takes one chain per lane.
+    for (int k0 = 0; k0 < total; k0 += 64) {
+        const int k = k0 + lane;
+        if (total - k0 > 32) {
+            const uint32_t e1 = ent[k];
+            const bool two = k + 32 < total;
+            const uint32_t e2 = two ? ent[k + 32] : e1;
+            const uint32_t r1i = e1 >> 5, p1 = e1 & 31u, r2i = e2 >> 5, p2 = e2 & 31u;  // record = task*32 + lane
+            uint32_t r1, r2;
+            if (RK) philox2_w0_rk(sites[r1i] + p1, sites[r2i] + p2, dk, rk, r1, r2);
+            else philox2_w0_key(sites[r1i] + p1, sites[r2i] + p2, dk, r1, r2);
+            const uint4 a = planes[r1i], b = planes[r2i];
+            const uint32_t Sa = ((a.x >> p1) & 1u) | (((a.y >> p1) & 1u) << 1) | (((a.z >> p1) & 1u) << 2) |
+                                (((a.w >> p1) & 1u) << 3);
+            const uint32_t Sb = ((b.x >> p2) & 1u) | (((b.y >> p2) & 1u) << 1) | (((b.z >> p2) & 1u) << 2) |
+                                (((b.w >> p2) & 1u) << 3);
+            if ((uint64_t)r1 < thr[Sa]) atomicOr(wacc + r1i, 1u << p1);
+            if (two && (uint64_t)r2 < thr[Sb]) atomicOr(wacc + r2i, 1u << p2);
+        } else if (k < total) {
+            const uint32_t e1 = ent[k];
+            const uint32_t r1i = e1 >> 5, p1 = e1 & 31u;
+            const uint32_t r1 = RK ? philox_w0_rk(sites[r1i] + p1, dk, rk) : philox_w0_key(sites[r1i] + p1, dk);
+            const uint4 a = planes[r1i];
+            const uint32_t Sa = ((a.x >> p1) & 1u) | (((a.y >> p1) & 1u) << 1) | (((a.z >> p1) & 1u) << 2) |
+                                (((a.w >> p1) & 1u) << 3);
+            if ((uint64_t)r1 < thr[Sa]) atomicOr(wacc + r1i, 1u << p1);
+        }
     }
     __syncwarp();
     acc0 = wacc[lane];

@@ -70,6 +70,12 @@ __device__ __forceinline__ void xor_word(uint32_t addr, uint32_t rank, bool loca
     }
 }
 
+// XOR v into the 32-bit word at shared address addr of this CTA, unconditionally.
+__device__ __forceinline__ void red_xor_local(uint32_t addr, uint32_t v)
+{
+    asm volatile("red.shared.xor.b32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+}
+
 // XOR mask into padded bit positions q .. q+31 of the row at shared address row (clipped).
 __device__ __forceinline__ void xor_at(uint32_t row, int RW, int q, uint32_t mask, uint32_t rank,
                                        bool local)
@@ -395,13 +401,14 @@ __device__ __forceinline__ void band_task_finish(const Geo &g, const TaskPrep &T
         const uint32_t wa = g.lat_addr + rowbytes * (uint32_t)lr + 4u * (uint32_t)(j + 1);
         const uint32_t wbw = wa + rowbytes * (uint32_t)bdy;
         const uint32_t lo = (uint32_t)mb, hi = (uint32_t)(mb >> 32);
+        // every word is XORed, zero or not: an atomic of 0 costs less than a branch
         if (bdy == 0) {
-            xor_word(wa, 0u, true, acc | lo);
+            red_xor_local(wa, acc | lo);
         } else {
-            xor_word(wa, 0u, true, acc);
-            xor_word(wbw, 0u, true, lo);
+            red_xor_local(wa, acc);
+            red_xor_local(wbw, lo);
         }
-        xor_word(wbw + 4u, 0u, true, hi);
+        red_xor_local(wbw + 4u, hi);
         return;
     }
     const uint32_t ra = g.lat_addr + rowbytes * (uint32_t)lr;
@@ -415,10 +422,10 @@ __device__ __forceinline__ void band_task_finish(const Geo &g, const TaskPrep &T
     if (wrap0) flip_row(g, rb, 0, 1ull, 0u, true);
 }
 
-template <int G, int OI, int THREADS>
+template <int G, int OI, int THREADS, bool RK>
 __device__ __forceinline__ void run_phase_pair(const uint32_t *lat, const Geo &g, const PhaseR &P,
                                                const uint64_t *thr, int f, uint32_t s_lo, uint32_t s_hi,
-                                               Acc &A, uint32_t *q, const TaskTab *tt)
+                                               Acc &A, uint32_t *q, const TaskTab *tt, const uint32_t (&rk)[2][8])
 {
     const int lane = threadIdx.x & 31;
     const int ntask = P.ntask;
@@ -430,20 +437,20 @@ __device__ __forceinline__ void run_phase_pair(const uint32_t *lat, const Geo &g
         band_task_prep<G, OI>(lat, g, P, use_tab, tt, ta, ta < ntask, T0, A);
         band_task_prep<G, OI>(lat, g, P, use_tab, tt, tb, tb < ntask, T1, A);
         uint32_t a0, a1;
-        draw_accepts_queue2(T0.dmask, T0.S, T0.base, T1.dmask, T1.S, T1.base, dk, thr, q, a0, a1);
+        draw_accepts_queue2<RK>(T0.dmask, T0.S, T0.base, T1.dmask, T1.S, T1.base, dk, rk, thr, q, a0, a1);
         band_task_finish<OI>(g, T0, T0.acc | a0, A);
         band_task_finish<OI>(g, T1, T1.acc | a1, A);
     }
 }
 
-template <int G, int THREADS>
+template <int G, int THREADS, bool RK>
 __device__ __forceinline__ void run_phase_pair_oi(const uint32_t *lat, const Geo &g, const PhaseR &P,
                                                   const uint64_t *thr, int f, uint32_t s_lo, uint32_t s_hi,
-                                                  Acc &A, uint32_t *q, const TaskTab *tt)
+                                                  Acc &A, uint32_t *q, const TaskTab *tt, const uint32_t (&rk)[2][8])
 {
-    if (P.oi == 0) run_phase_pair<G, 0, THREADS>(lat, g, P, thr, f, s_lo, s_hi, A, q, tt);
-    else if (G == kTRI6 && P.oi == 2) run_phase_pair<G, 2, THREADS>(lat, g, P, thr, f, s_lo, s_hi, A, q, tt);
-    else run_phase_pair<G, 1, THREADS>(lat, g, P, thr, f, s_lo, s_hi, A, q, tt);
+    if (P.oi == 0) run_phase_pair<G, 0, THREADS, RK>(lat, g, P, thr, f, s_lo, s_hi, A, q, tt, rk);
+    else if (G == kTRI6 && P.oi == 2) run_phase_pair<G, 2, THREADS, RK>(lat, g, P, thr, f, s_lo, s_hi, A, q, tt, rk);
+    else run_phase_pair<G, 1, THREADS, RK>(lat, g, P, thr, f, s_lo, s_hi, A, q, tt, rk);
 }
 
 template <int G, int THREADS, bool BLOCKED>
@@ -894,9 +901,9 @@ band_phases_kernel(const SweepJob J, const void *__restrict__ src, void *__restr
         const TaskTab T = {t, (int2 *)(t + tab_w), g.W, tab_rows};
         const TaskTab *const tt = tables ? &T : nullptr;
         if (J.geometry == kTRI6)
-            run_phase_pair_oi<kTRI6, THREADS>(lat, g, P, thr, f0 + j, s_lo, s_hi, A, dq, tt);
+            run_phase_pair_oi<kTRI6, THREADS, true>(lat, g, P, thr, f0 + j, s_lo, s_hi, A, dq, tt, J.rk);
         else
-            run_phase_pair_oi<kSQ4, THREADS>(lat, g, P, thr, f0 + j, s_lo, s_hi, A, dq, tt);
+            run_phase_pair_oi<kSQ4, THREADS, true>(lat, g, P, thr, f0 + j, s_lo, s_hi, A, dq, tt, J.rk);
         __syncthreads();
     }
 
