@@ -11,7 +11,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libklmc.so")
-SOURCES = ["sweep_resident.cu", "sweep_tiled.cu", "sweep_mpkk.cu", "lattice_ops.cu", "clusters.cu",
+SOURCES = ["sweep_resident.cu", "sweep_tiled.cu", "sweep_mpkk.cu", "sweep_helical.cu", "lattice_ops.cu", "clusters.cu",
            "clusters_noalloc.cu", "images.cu", "api.cu", "server.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -110,9 +110,12 @@ klmc_status validate(const klmc_params *p)
         if (!helical_tiles(p->Lx, p->Ly))
             return fail(KLMC_EINVAL, "helical lattice: seven-site domains tile it only when 7 divides Lx*Ly "
                                      "and Lx mod 7 is 3 or 5");
-        if (p->cluster > 0 || p->threads != 0)
-            return fail(KLMC_EINVAL, "helical lattices run one launch per iteration; cluster and threads "
-                                     "must be 0 (or cluster -1)");
+        if (p->threads != 0 && p->threads != 512)
+            return fail(KLMC_EINVAL, "helical lattices run at 512 threads per CTA (threads 0 or 512)");
+        if (p->cluster > 0 && helical_resident_block(p->Lx, p->Ly, p->cluster) < 2)
+            return fail(KLMC_EINVAL, "helical lattice: the resident sweep needs a cluster of at least 2 CTAs "
+                                     "whose bands each hold 2K+1 halo rows for K >= 2 iterations per block "
+                                     "(cluster 0 chooses, cluster -1 runs one launch per iteration)");
     }
     if (p->packing != KLMC_PACK_AUTO && p->packing != KLMC_PACK_BIT && p->packing != KLMC_PACK_BYTE)
         return fail(KLMC_EINVAL, "unknown packing");
@@ -215,8 +218,11 @@ klmc_status create_one(klmc_ctx **out, const klmc_params *p, klmc_batch *owner, 
     c->W = (p->Lx + 31) / 32;
     c->helical = p->boundary == KLMC_HELICAL;
     if (c->helical) {
-        c->cluster = -1;  // one launch per iteration over the device store
-        c->threads = 256;
+        // Resident in a cluster's shared memory when the bands are tall enough for
+        // blocks of iterations; otherwise one launch per iteration over the store.
+        c->cluster = p->cluster != 0 ? p->cluster : auto_cluster(p->Lx, p->Ly);
+        if (c->cluster > 0 && helical_resident_block(p->Lx, p->Ly, c->cluster) < 2) c->cluster = -1;
+        c->threads = c->cluster > 0 ? 512 : 256;
         c->auto_shape = false;
     } else {
         c->cluster = p->cluster != 0 ? p->cluster : auto_cluster(p->Lx, p->Ly);
@@ -396,6 +402,18 @@ klmc_status sweep_one(klmc_ctx *c, int64_t n_mcs, int64_t trace_every, int64_t *
         return fail(KLMC_EINVAL, "trace_every > 0 needs a device trace buffer");
     if (n_mcs == 0) return KLMC_OK;
     if (c->cluster < 0) return sweep_tiled(c, n_mcs, trace_every, dev_trace);
+    if (c->helical) {
+        if (trace_every > 0 && n_mcs / trace_every > 0)
+            KLMC_CUDA(cudaMemsetAsync(dev_trace, 0, (size_t)(n_mcs / trace_every) * sizeof(int64_t), c->stream));
+        SweepCall call;
+        call.sweep0 = c->sweep;
+        call.n_mcs = n_mcs;
+        call.trace = (long long *)dev_trace;
+        call.trace_every = trace_every;
+        KLMC_CUDA(launch_helical_resident(c->job, call, c->cluster, c->stream));
+        c->sweep += n_mcs;
+        return KLMC_OK;
+    }
     klmc_status st = check_resident(c, c->cluster);
     if (st != KLMC_OK) return st;
     if (trace_every > 0 && n_mcs / trace_every > 0)
@@ -937,7 +955,8 @@ klmc_status klmc_get_plan(klmc_ctx *c, int32_t *phases_per_exchange)
 {
     if (!c || !phases_per_exchange) return fail(KLMC_EINVAL, "NULL argument");
     if (c->cluster > 0) {
-        *phases_per_exchange = resident_block_phases(c->p.Lx, c->p.Ly, c->cluster);
+        *phases_per_exchange = c->helical ? helical_resident_block(c->p.Lx, c->p.Ly, c->cluster)
+                                          : resident_block_phases(c->p.Lx, c->p.Ly, c->cluster);
         return KLMC_OK;
     }
     if (c->helical) {

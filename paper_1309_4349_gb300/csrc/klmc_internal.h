@@ -121,6 +121,12 @@ cudaError_t launch_image_ffn(const uint8_t *image, const uint8_t *mask, int W, i
 // iteration launches of each of n_sweeps sweeps k0 .. (sweep index from
 // state[kSweepBase]).
 bool helical_tiles(int Lx, int Ly);
+// Resident helical sweep (sweep_helical.cu): iterations per block of a helical
+// lattice over `cluster` CTAs (0: not resident), its dynamic shared memory, and one
+// launch of n_mcs sweeps, one cluster of `cluster` CTAs of 512 threads.
+int helical_resident_block(int Lx, int Ly, int cluster);
+size_t helical_resident_smem_bytes(int Lx, int Ly, int cluster);
+cudaError_t launch_helical_resident(const SweepJob &job, const SweepCall &call, int cluster, cudaStream_t stream);
 cudaError_t launch_mpkk_phases(const SweepJob &job, int k0, int n_sweeps, int sm_count, cudaStream_t stream);
 
 // Initial placement: the nA sites with the smallest (64-bit Philox key, index).

@@ -18,9 +18,9 @@ import paper_1309_4349_gb300 as klmc  # noqa: E402
 klmc.build()
 
 
-def make(Lx, Ly, nA, bw, seed, packing=klmc.PACK_BIT):
+def make(Lx, Ly, nA, bw, seed, packing=klmc.PACK_BIT, cluster=0):
     return klmc.Lattice(Lx, Ly, geometry=klmc.TRI6, packing=packing, n_A=nA, omega_over_kT=bw, seed=seed,
-                        boundary=klmc.HELICAL)
+                        boundary=klmc.HELICAL, cluster=cluster)
 
 
 def assert_same_run(lat, ref, Lx, Ly):
@@ -32,14 +32,22 @@ def assert_same_run(lat, ref, Lx, Ly):
                                                                    oracle.HELICAL)
 
 
+@pytest.mark.parametrize("cluster", [0, -1])
 @pytest.mark.parametrize("packing", [klmc.PACK_BIT, klmc.PACK_BYTE])
 @pytest.mark.parametrize("Lx,Ly,bw,n_mcs", [(10, 7, 0.9, 23), (12, 14, -0.5, 17), (17, 7, 0.0, 9),
                                             (24, 21, 1.4, 13), (40, 35, 0.6, 11), (402, 399, 0.8, 5)])
-def test_helical_parity(packing, Lx, Ly, bw, n_mcs):
+def test_helical_parity(cluster, packing, Lx, Ly, bw, n_mcs):
+    """Automatic shape (resident in a cluster when the bands are tall enough for
+    blocks of iterations, else one launch per iteration) and the per-iteration
+    path, both against the oracle."""
     assert oracle.helical_valid(Lx, Ly)
     nA, seed = Lx * Ly * 3 // 10, 11 + Lx
-    lat = make(Lx, Ly, nA, bw, seed, packing)
-    assert lat.launch_shape()[0] == -1 and lat.plan() == 1
+    lat = make(Lx, Ly, nA, bw, seed, packing, cluster)
+    C, T = lat.launch_shape()
+    if cluster == -1 or Ly < 48:
+        assert C == -1 and lat.plan() == 1
+    else:
+        assert C >= 2 and T == 512 and lat.plan() in (2, 4)
     t0 = lat.get_lattice()
     assert np.array_equal(t0, oracle.init(Lx, Ly, nA, seed))
     assert lat.energy()[0] == oracle.n_unlike(Lx, Ly, oracle.TRI6, t0, oracle.HELICAL)
@@ -133,3 +141,46 @@ def test_c6_workload_one_run_full():
             assert abs(got - want) <= 1e-12 * abs(want), k
     assert_same_run(lat, r, Lx, Ly)
     lat.close()
+
+
+@pytest.mark.parametrize("packing", [klmc.PACK_BIT, klmc.PACK_BYTE])
+@pytest.mark.parametrize("Lx,Ly,cluster,bw", [(101, 98, 4, 0.7), (101, 98, 2, -0.6), (103, 70, 2, 1.2),
+                                              (199, 77, 4, 0.0), (199, 77, 8, 0.9), (38, 336, 16, 0.5),
+                                              (402, 399, 16, 1.0), (402, 399, 8, 0.3)])
+def test_helical_resident_parity(packing, Lx, Ly, cluster, bw):
+    """The resident helical sweep (a cluster of CTAs, blocks of iterations with
+    re-evaluated halos, pads of the helical row continuation) at explicit cluster
+    sizes, both stores, rows of one to thirteen words with ragged ends, both
+    residues of Lx mod 7: against the oracle over several calls whose iterations
+    cross sweep and block boundaries."""
+    assert oracle.helical_valid(Lx, Ly)
+    nA, seed = Lx * Ly // 3, 40 + cluster
+    lat = make(Lx, Ly, nA, bw, seed, packing, cluster)
+    assert lat.launch_shape() == (cluster, 512)
+    t0 = lat.get_lattice()
+    for n in (1, 3, 7):
+        lat.sweep(n)
+    ref = oracle.run_mpkk(Lx, Ly, bw, seed, t0, 0, 11)
+    assert_same_run(lat, ref, Lx, Ly)
+
+
+def test_helical_resident_equals_per_iteration_path():
+    """The same lattice and seed on the resident sweep and on one launch per
+    iteration: identical lattices, counters and traces after 40 steps."""
+    Lx, Ly, bw, seed = 402, 399, 0.6, 4
+    nA = Lx * Ly * 3 // 10
+    a = make(Lx, Ly, nA, bw, seed, cluster=16)
+    b = make(Lx, Ly, nA, bw, seed, cluster=-1)
+    ta = a.sweep_traced(40, 5)
+    tb = b.sweep_traced(40, 5)
+    torch.cuda.synchronize()
+    assert ta.cpu().numpy().tolist() == tb.cpu().numpy().tolist()
+    assert np.array_equal(a.get_lattice(), b.get_lattice())
+    assert a.counters() == b.counters()
+    assert a.energy() == b.energy()
+
+
+def test_helical_resident_rejects_thin_bands():
+    with pytest.raises(klmc.KlmcError) as e:
+        make(103, 70, 1000, 0.5, 1, cluster=16)  # bands of 4 rows: no room for 2K+1 halo rows
+    assert e.value.status == 1
