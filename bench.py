@@ -744,19 +744,23 @@ def sub_c6(x):
     draws = sum(c_["draws"] for c_ in cnts)
     assert attempts == len(lats) * c["mcs"] * Lx * Ly
     ms_step = sum(ms) / len(ms)
-    C, _ = lats[0].launch_shape()
-    iters = 7 * c["mcs"]
+    C, T = lats[0].launch_shape()
     lat_bytes = Ly * ((Lx + 31) // 32) * 4
+    resident = C > 0
     out = {"value": attempts / (ms_step * 1e-3), "unit": "attempts/s", "ms_per_step": ms_step,
            "config": {"workload": "helical triangular 402x399 (7 | N, 402 mod 7 = 3), seven-colour MPKK "
                                   "schedule, 30% A random start, omega/kT in {0.2,0.4,0.6,0.8,1.0} (5 runs, "
                                   "seeds 2..6), 2000 MCS each, A-cluster histogram every 500 MCS, 1 bit/site",
-                      "form": "the 5 lattices on 5 streams", "l2": "flushed between steps"},
-           "roofline": _roofline("mpkk sweep", ms_step, attempts, draws / attempts, x.sm_count, _sm_mhz(clk),
-                                 C, 2 * len(lats) * iters * lat_bytes, x.l2_peak,
+                      "form": (f"the 5 lattices on 5 streams, each resident in a {C}-CTA cluster of {T} threads"
+                               if resident else "the 5 lattices on 5 streams, one launch per iteration"),
+                      "l2": "flushed between steps"},
+           "roofline": _roofline("helical_resident_kernel" if resident else "mpkk_phase_kernel", ms_step, attempts,
+                                 draws / attempts, x.sm_count, _sm_mhz(clk), len(lats) * max(C, 1),
+                                 (2 * len(lats) * nseg * lat_bytes if resident
+                                  else 2 * len(lats) * 7 * c["mcs"] * lat_bytes), x.l2_peak,
                                  {"note": "all launches of a step, the 5 lattices' overlapping on 5 streams: "
-                                          "time = step time; L2 bytes: the lattice read and written once per "
-                                          "iteration"}),
+                                          "time = step time; L2 bytes: each lattice in and out once per "
+                                          "resident launch (once per iteration on the per-iteration path)"}),
            "clocks": clk}
     for l_ in lats:
         l_.close()

@@ -68,9 +68,13 @@ typedef struct klmc_params {
                               neighbours) tile the lattice, which requires TRI6,
                               7 | Lx*Ly and Lx mod 7 in {3, 5} (else EINVAL);
                               each step is 7 iterations, each drawing k in 0..6
-                              and one direction for all domains; one launch per
-                              iteration over the device store (cluster and threads
-                              must be 0); not in batches or the server           */
+                              and one direction for all domains.  Lattices whose
+                              bands over a cluster of CTAs hold the halo rows of
+                              blocks of iterations run resident in the cluster's
+                              shared memory (512 threads per CTA; in handles,
+                              batches and the server); smaller ones run one
+                              launch per iteration over the device store (cluster
+                              -1; handles only)                                   */
     int32_t packing;       /* device store: KLMC_PACK_BIT (1 bit/site), _BYTE, or
                               _AUTO (= BIT)                                       */
     int32_t cluster;       /* CTAs that share one lattice in the resident sweep
@@ -324,7 +328,9 @@ klmc_status klmc_destroy(klmc_ctx *c);
  * launches of different shapes run on internal streams forked from and joined
  * back to the stream of reps[0], which every replica uses.  The trajectory of a
  * replica does not depend on its launch shape.  Every replica must fit the
- * shared-memory resident sweep. */
+ * shared-memory resident sweep; a helical replica (KLMC_HELICAL) runs the resident
+ * helical sweep, one launch of its own cluster on an internal stream, alongside
+ * the others. */
 klmc_status klmc_batch_create(klmc_batch **out, const klmc_params *reps, int32_t n);
 
 /* Enqueues n_mcs[i] steps for replica i (entries may differ; 0 skips). */
@@ -395,7 +401,9 @@ klmc_status klmc_server_create(klmc_server **out, size_t device_mem_budget, void
  * server's worker thread, and a NULL from alloc fails the job with KLMC_ENOMEM), n_mcs
  * steps, an A-cluster histogram every hist_every steps and at the end
  * (0: none), flags (KLMC_JOB_KEEP_LATTICE).  Thread-safe; never blocks on GPU work.
- * Jobs too large for the budget finish with status KLMC_EINVAL. */
+ * Jobs too large for the budget, or too large for a cluster's shared memory, and
+ * helical lattices too small for the resident helical sweep, finish with status
+ * KLMC_EINVAL.  A helical job runs the resident helical sweep, one launch per round. */
 klmc_status klmc_server_submit(klmc_server *s, const klmc_params *p, int64_t n_mcs,
                                int64_t hist_every, uint32_t flags, uint64_t *job_id);
 

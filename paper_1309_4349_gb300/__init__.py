@@ -476,12 +476,13 @@ class Server:
     def submit(self, Lx: int, Ly: int | None = None, *, n_mcs: int, hist_every: int = 0,
                keep_lattice: bool = False, geometry: int = TRI6, packing: int = PACK_BIT,
                n_A: int = -1, fraction_A: float = 0.5, omega_over_kT: float = 0.0, seed: int = 1,
-               cluster: int = 0, allocator=None) -> int:
+               cluster: int = 0, boundary: int = 0, allocator=None) -> int:
         """Queues a job; `allocator` (an object with ``alloc`` and ``free`` callbacks
         of types ALLOC_FN and FREE_FN, kept alive by the caller until the job ends)
         serves the job's lattice memory instead of the server's own allocations."""
         p = make_params(Lx, Ly, geometry=geometry, packing=packing, n_A=n_A, fraction_A=fraction_A,
-                        omega_over_kT=omega_over_kT, seed=seed, cluster=cluster, allocator=allocator)
+                        omega_over_kT=omega_over_kT, seed=seed, cluster=cluster, boundary=boundary,
+                        allocator=allocator)
         jid = ctypes.c_uint64()
         _check(lib().klmc_server_submit(self._h, ctypes.byref(p), int(n_mcs), int(hist_every),
                                         JOB_KEEP_LATTICE if keep_lattice else 0, ctypes.byref(jid)))

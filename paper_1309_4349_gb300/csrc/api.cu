@@ -997,11 +997,12 @@ klmc_status klmc_batch_create(klmc_batch **out, const klmc_params *reps, int32_t
         p.stream = reps[0].stream;
         klmc_ctx *c = nullptr;
         klmc_status st = create_one(&c, &p, b);
-        if (st == KLMC_OK && c->helical)
-            st = fail(KLMC_EINVAL, "helical lattices run on the per-handle path, not in batches");
+        if (st == KLMC_OK && c->helical && c->cluster < 0)
+            st = fail(KLMC_EINVAL, "helical lattice whose bands are too thin for the resident sweep: it runs "
+                                   "one launch per iteration, on its own handle");
         else if (st == KLMC_OK && c->cluster < 0)
             st = fail(KLMC_EINVAL, "lattice too large for a batched resident launch");
-        if (st == KLMC_OK) st = check_resident(c, c->cluster);
+        if (st == KLMC_OK && !c->helical) st = check_resident(c, c->cluster);
         if (st != KLMC_OK) {
             std::string msg = "replica " + std::to_string(i) + ": " + g_err;
             if (c) {
@@ -1053,7 +1054,7 @@ klmc_status klmc_batch_sweep(klmc_batch *b, const int64_t *n_mcs)
     const int n = (int)b->reps.size();
     std::vector<klmc_ctx *> active;
     std::vector<int64_t> active_steps;
-    std::vector<int> index;
+    std::vector<int> index, helical;
     for (int i = 0; i < n; ++i) {
         if (n_mcs[i] < 0) return fail(KLMC_EINVAL, "n_mcs entries must be >= 0");
         klmc_ctx *c = b->reps[i];
@@ -1062,13 +1063,42 @@ klmc_status klmc_batch_sweep(klmc_batch *b, const int64_t *n_mcs)
         call.n_mcs = n_mcs[i];
         call.trace = nullptr;
         call.trace_every = 0;
-        if (n_mcs[i] > 0) {
+        if (n_mcs[i] > 0 && c->helical) {
+            helical.push_back(i);
+        } else if (n_mcs[i] > 0) {
             active.push_back(c);
             active_steps.push_back(n_mcs[i]);
             index.push_back(i);
         }
     }
-    if (active.empty()) return KLMC_OK;
+    if (active.empty() && helical.empty()) return KLMC_OK;
+    KLMC_CUDA(cudaEventRecord(b->fork, b->stream));
+    // Helical replicas: the resident helical sweep, one launch each on a stream of its
+    // own (key (-1 - i, 512) in the group-stream map), overlapping the others; joined
+    // back to the batch stream after the other launches are enqueued.
+    std::vector<cudaEvent_t> joins;
+    for (int i : helical) {
+        const std::pair<int, int> key(-1 - i, 512);
+        auto it = b->group_streams.find(key);
+        if (it == b->group_streams.end()) {
+            cudaStream_t gs;
+            cudaEvent_t ge;
+            KLMC_CUDA(cudaStreamCreateWithFlags(&gs, cudaStreamNonBlocking));
+            KLMC_CUDA(cudaEventCreateWithFlags(&ge, cudaEventDisableTiming));
+            it = b->group_streams.emplace(key, std::make_pair(gs, ge)).first;
+        }
+        klmc_ctx *c = b->reps[i];
+        b->last_shape[i] = {c->cluster, 512};
+        KLMC_CUDA(cudaStreamWaitEvent(it->second.first, b->fork, 0));
+        KLMC_CUDA(launch_helical_resident(c->job, b->hcalls[i], c->cluster, it->second.first));
+        KLMC_CUDA(cudaEventRecord(it->second.second, it->second.first));
+        joins.push_back(it->second.second);
+    }
+    if (active.empty()) {
+        for (cudaEvent_t ev : joins) KLMC_CUDA(cudaStreamWaitEvent(b->stream, ev, 0));
+        for (int i = 0; i < n; ++i) b->reps[i]->sweep += n_mcs[i];
+        return KLMC_OK;
+    }
     // One launch per launch shape, each on its own stream (the launches overlap on
     // the GPU), larger lattices first inside a launch.
     std::vector<std::pair<int, int>> shapes;
@@ -1089,7 +1119,7 @@ klmc_status klmc_batch_sweep(klmc_batch *b, const int64_t *n_mcs)
                               cudaMemcpyHostToDevice, b->stream));
     KLMC_CUDA(cudaMemcpyAsync(b->dmap, hmap.data(), sizeof(int) * hmap.size(), cudaMemcpyHostToDevice,
                               b->stream));
-    KLMC_CUDA(cudaEventRecord(b->fork, b->stream));
+    KLMC_CUDA(cudaEventRecord(b->fork, b->stream));  // after the tables' upload
     int offset = 0;
     for (auto &g : groups) {
         auto it = b->group_streams.find(g.first);
@@ -1114,6 +1144,7 @@ klmc_status klmc_batch_sweep(klmc_batch *b, const int64_t *n_mcs)
         KLMC_CUDA(cudaStreamWaitEvent(b->stream, it->second.second, 0));
         offset += (int)g.second.size();
     }
+    for (cudaEvent_t ev : joins) KLMC_CUDA(cudaStreamWaitEvent(b->stream, ev, 0));
     for (int i = 0; i < n; ++i) b->reps[i]->sweep += n_mcs[i];
     return KLMC_OK;
 }
@@ -1164,7 +1195,8 @@ klmc_status klmc_batch_cluster_histogram_device(klmc_batch *b, int32_t species, 
         KLMC_CUDA(launch_cluster_histogram(c->lat, c->job.packing, c->p.Lx, c->p.Ly, c->pitch, c->p.geometry,
                                            species, c->cs, capacity ? (long long *)dev_sizes + off : nullptr,
                                            capacity ? (long long *)dev_counts + off : nullptr, capacity,
-                                           (long long *)dev_n_distinct + i, b->hist_streams[i % ns].first));
+                                           (long long *)dev_n_distinct + i, b->hist_streams[i % ns].first,
+                                           c->helical));
     }
     for (int k = 0; k < ns; ++k) {
         KLMC_CUDA(cudaEventRecord(b->hist_streams[k].second, b->hist_streams[k].first));

@@ -89,6 +89,8 @@ double seconds(const klmc_server *s) { return std::chrono::duration<double>(Cloc
 
 // Steps per round: about 4 ms of work for every job at the launch shape it runs
 // with this round.
+constexpr int kHelicalStreams = 8;  // streams for the helical jobs of a round
+
 int64_t quantum(const Job *j, std::pair<int, int> shape)
 {
     const klmc_ctx *c = j->ctx;
@@ -190,8 +192,9 @@ int admit(klmc_server *s)
             s->pending.pop_front();
         }
         klmc_status st = klmc::host::create_async(&j->ctx, &p);
-        if (st == KLMC_OK && j->ctx->helical)
-            st = fail(KLMC_EINVAL, "helical lattices run on the per-handle path, not in the server");
+        if (st == KLMC_OK && j->ctx->helical && j->ctx->cluster < 0)
+            st = fail(KLMC_EINVAL, "helical lattice whose bands are too thin for the resident sweep: it runs "
+                                   "one launch per iteration, on its own handle");
         else if (st == KLMC_OK && j->ctx->cluster < 0)
             st = fail(KLMC_EINVAL, "lattice too large for the resident sweep");
         if (st != KLMC_OK) {
@@ -236,14 +239,24 @@ klmc_status run_round(klmc_server *s)
     std::vector<klmc::SweepCall> hcalls(n);
     std::vector<int64_t> q(n);
     std::map<std::pair<int, int>, std::vector<int>> groups;
-    std::vector<klmc_ctx *> ctxs(n);
-    std::vector<int64_t> remaining(n);
+    // Periodic jobs share launches by shape; helical jobs run the resident helical
+    // sweep, one launch each.
+    std::vector<klmc_ctx *> ctxs;
+    std::vector<int64_t> remaining;
+    std::vector<int> periodic, helical;
     for (int i = 0; i < n; ++i) {
-        ctxs[i] = s->active[i]->ctx;
-        remaining[i] = s->active[i]->n_mcs - s->active[i]->done;
+        if (s->active[i]->ctx->helical) {
+            helical.push_back(i);
+            continue;
+        }
+        periodic.push_back(i);
+        ctxs.push_back(s->active[i]->ctx);
+        remaining.push_back(s->active[i]->n_mcs - s->active[i]->done);
     }
-    std::vector<std::pair<int, int>> shapes;
-    klmc::host::choose_shapes(ctxs, remaining, s->sm_count, true, &shapes);
+    std::vector<std::pair<int, int>> pshapes, shapes(n);
+    klmc::host::choose_shapes(ctxs, remaining, s->sm_count, true, &pshapes);
+    for (size_t k = 0; k < periodic.size(); ++k) shapes[periodic[k]] = pshapes[k];
+    for (int i : helical) shapes[i] = {s->active[i]->ctx->cluster, 512};
     for (int i = 0; i < n; ++i) {
         Job *j = s->active[i];
         q[i] = quantum(j, shapes[i]);
@@ -252,7 +265,7 @@ klmc_status run_round(klmc_server *s)
         hcalls[i].n_mcs = q[i];
         hcalls[i].trace = nullptr;
         hcalls[i].trace_every = 0;
-        groups[shapes[i]].push_back(i);
+        if (!j->ctx->helical) groups[shapes[i]].push_back(i);
     }
     std::vector<int> hmap;
     hmap.reserve(n);
@@ -267,8 +280,29 @@ klmc_status run_round(klmc_server *s)
         e = cudaMemcpyAsync(s->dcalls, hcalls.data(), sizeof(klmc::SweepCall) * (size_t)n,
                             cudaMemcpyHostToDevice, s->stream);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(s->dmap, hmap.data(), sizeof(int) * (size_t)n, cudaMemcpyHostToDevice, s->stream);
+        e = hmap.empty() ? cudaSuccess
+                         : cudaMemcpyAsync(s->dmap, hmap.data(), sizeof(int) * hmap.size(), cudaMemcpyHostToDevice,
+                                           s->stream);
     if (e == cudaSuccess) e = cudaEventRecord(s->fork, s->stream);
+    // Helical jobs on a pool of kHelicalStreams streams (keys (-1 - k, 512)).
+    for (size_t k = 0; k < helical.size() && e == cudaSuccess; ++k) {
+        const int i = helical[k];
+        const std::pair<int, int> key(-1 - (int)(k % kHelicalStreams), 512);
+        auto it = s->group_streams.find(key);
+        if (it == s->group_streams.end()) {
+            cudaStream_t gs;
+            cudaEvent_t ge;
+            e = cudaStreamCreateWithFlags(&gs, cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ge, cudaEventDisableTiming);
+            if (e != cudaSuccess) break;
+            it = s->group_streams.emplace(key, std::make_pair(gs, ge)).first;
+        }
+        e = cudaStreamWaitEvent(it->second.first, s->fork, 0);
+        if (e == cudaSuccess)
+            e = klmc::launch_helical_resident(hjobs[i], hcalls[i], shapes[i].first, it->second.first);
+        if (e == cudaSuccess) e = cudaEventRecord(it->second.second, it->second.first);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s->stream, it->second.second, 0);
+    }
     int offset = 0;
     for (auto &g : groups) {
         if (e != cudaSuccess) break;
@@ -308,7 +342,7 @@ klmc_status run_round(klmc_server *s)
             e = klmc::launch_cluster_histogram(j->ctx->lat, j->ctx->job.packing, j->ctx->p.Lx,
                                                j->ctx->p.Ly, j->ctx->pitch, j->ctx->p.geometry, 1, s->cs,
                                                j->dhist, j->dhist + j->hist_cap, j->hist_cap,
-                                               j->dhist + 2 * j->hist_cap, s->stream);
+                                               j->dhist + 2 * j->hist_cap, s->stream, j->ctx->helical);
             j->n_hist += 1;
         }
         if (last) finishing.push_back(j);

@@ -184,3 +184,77 @@ def test_helical_resident_rejects_thin_bands():
     with pytest.raises(klmc.KlmcError) as e:
         make(103, 70, 1000, 0.5, 1, cluster=16)  # bands of 4 rows: no room for 2K+1 halo rows
     assert e.value.status == 1
+
+
+def test_helical_replicas_in_a_batch():
+    """Helical replicas (resident helical sweep, one launch each) batched with
+    periodic ones: every replica equals its own oracle run, and the batch's
+    histograms of the helical replicas use the helical adjacency."""
+    reps = [dict(Lx=101, Ly=98, n_A=3000, omega_over_kT=0.8, seed=61, boundary=klmc.HELICAL),
+            dict(Lx=120, Ly=100, n_A=4000, omega_over_kT=0.6, seed=62),
+            dict(Lx=402, Ly=399, n_A=48000, omega_over_kT=1.0, seed=63, boundary=klmc.HELICAL),
+            dict(Lx=64, Ly=64, n_A=2048, omega_over_kT=0.4, seed=64, geometry=klmc.SQ4)]
+    b = klmc.Batch(reps)
+    inits = [lat.get_lattice() for lat in b.replicas]
+    steps = [9, 7, 5, 3]
+    b.sweep(steps)
+    for r, lat, t0, n in zip(reps, b.replicas, inits, steps):
+        Lx, Ly = r["Lx"], r["Ly"]
+        if r.get("boundary") == klmc.HELICAL:
+            assert b.launch_shape(reps.index(r))[1] == 512
+            ref = oracle.run_mpkk(Lx, Ly, r["omega_over_kT"], r["seed"], t0, 0, n)
+            assert_same_run(lat, ref, Lx, Ly)
+        else:
+            ref = oracle.run(Lx, Ly, r.get("geometry", klmc.TRI6), r["omega_over_kT"], r["seed"], t0, 0, n)
+            assert np.array_equal(lat.get_lattice(), ref.lattice)
+            assert lat.energy()[0] == ref.n_unlike
+    cap = 512
+    sizes = torch.zeros((len(reps), cap), dtype=torch.int64, device="cuda")
+    counts = torch.zeros_like(sizes)
+    nd = torch.zeros(len(reps), dtype=torch.int64, device="cuda")
+    b.cluster_histogram_device(1, sizes, counts, nd)
+    torch.cuda.synchronize()
+    for i, (r, lat) in enumerate(zip(reps, b.replicas)):
+        bnd = oracle.HELICAL if r.get("boundary") == klmc.HELICAL else oracle.PERIODIC
+        rs, rc = oracle.cluster_histogram(r["Lx"], r["Ly"], r.get("geometry", klmc.TRI6), lat.get_lattice(), 1,
+                                          bnd)
+        k = int(nd[i].item())
+        assert k == rs.size
+        assert np.array_equal(sizes[i, :k].cpu().numpy(), rs) and np.array_equal(counts[i, :k].cpu().numpy(), rc)
+    b.close()
+
+
+def test_helical_jobs_in_the_server():
+    """Helical jobs served beside periodic ones: each result equals the oracle's
+    run of that job, histograms included; a helical lattice too small for the
+    resident sweep is refused as a job (EINVAL) without stopping the others."""
+    srv = klmc.Server(1 << 30)
+    jobs = [dict(L=(101, 98), helical=True, n_A=3000, w=0.7, seed=71, n=40),
+            dict(L=(96, 96), helical=False, n_A=3000, w=0.9, seed=72, n=30),
+            dict(L=(402, 399), helical=True, n_A=40000, w=1.1, seed=73, n=25),
+            dict(L=(10, 7), helical=True, n_A=20, w=0.5, seed=74, n=5)]
+    ids = [srv.submit(j["L"][0], j["L"][1], n_mcs=j["n"], hist_every=10, keep_lattice=True, n_A=j["n_A"],
+                      omega_over_kT=j["w"], seed=j["seed"], boundary=klmc.HELICAL if j["helical"] else 0)
+           for j in jobs]
+    srv.drain(300.0)
+    for j, jid in zip(jobs, ids):
+        r = srv.poll(jid)
+        Lx, Ly = j["L"]
+        if (Lx, Ly) == (10, 7):
+            assert r["status"] == 1
+            continue
+        assert r["status"] == 0
+        t0 = oracle.init(Lx, Ly, j["n_A"], j["seed"])
+        if j["helical"]:
+            ref = oracle.run_mpkk(Lx, Ly, j["w"], j["seed"], t0, 0, j["n"])
+            bnd = oracle.HELICAL
+        else:
+            ref = oracle.run(Lx, Ly, oracle.TRI6, j["w"], j["seed"], t0, 0, j["n"])
+            bnd = oracle.PERIODIC
+        assert np.array_equal(srv.lattice(jid, Lx * Ly), ref.lattice)
+        assert (r["attempts"], r["unlike"], r["draws"], r["accepts"]) == ref.counters()
+        assert r["n_unlike"] == ref.n_unlike
+        s, c = srv.histogram(jid)
+        rs, rc = oracle.cluster_histogram(Lx, Ly, oracle.TRI6, ref.lattice, 1, bnd)
+        assert np.array_equal(s, rs) and np.array_equal(c, rc)
+    srv.close()
