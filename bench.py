@@ -75,11 +75,14 @@ INT32_LANES_PER_SM = 64
 ISSUE_LANES_PER_SM = 128
 # DRAM bytes (read + write) per launch of the dominant kernel, from one ncu capture
 # each (one resident-sweep launch of 500 MCS of the 400x400 x 5 workload; one
-# 4-phase band launch of the 8192x8192 lattice), valid only for the kernel sources
-# they were taken with (hash of sweep_resident.cu + sweep_common.cuh + philox.cuh).
-TRAFFIC_C2_LAUNCH = None
-TRAFFIC_C3_LAUNCH = None
-TRAFFIC_SOURCES = ""
+# 4-phase band launch of the 8192x8192 lattice; one resident helical launch of 500
+# MCS of one 402x399 lattice), valid only for the kernel sources they were taken
+# with (hash of the kernel's file + sweep_common.cuh + philox.cuh).
+TRAFFIC_C2_LAUNCH = 222208
+TRAFFIC_C3_LAUNCH = 8500736
+TRAFFIC_SOURCES = "aff7c9aafc102963"
+TRAFFIC_C6_LAUNCH = 275968
+TRAFFIC_HELICAL_SOURCES = "6a258ca347341b5c"
 
 # Kernels launched per library call (fixed by the library's structure).
 LAUNCHES_SWEEP = 1
@@ -108,11 +111,11 @@ SUB_WARMUP = 3
 SUB_STEPS = 3
 
 
-def resident_sources_hash() -> str:
+def resident_sources_hash(kernel_file: str = "sweep_resident.cu") -> str:
     import hashlib
 
     h = hashlib.sha256()
-    for f in ("sweep_resident.cu", "sweep_common.cuh", "philox.cuh"):
+    for f in (kernel_file, "sweep_common.cuh", "philox.cuh"):
         with open(os.path.join(ROOT, "paper_1309_4349_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -760,7 +763,12 @@ def sub_c6(x):
                                   else 2 * len(lats) * 7 * c["mcs"] * lat_bytes), x.l2_peak,
                                  {"note": "all launches of a step, the 5 lattices' overlapping on 5 streams: "
                                           "time = step time; L2 bytes: each lattice in and out once per "
-                                          "resident launch (once per iteration on the per-iteration path)"}),
+                                          "resident launch (once per iteration on the per-iteration path)",
+                                  "traffic": (len(lats) * nseg * TRAFFIC_C6_LAUNCH if resident and
+                                              resident_sources_hash("sweep_helical.cu") == TRAFFIC_HELICAL_SOURCES
+                                              and c["hist_every"] == 500 else None),
+                                  "traffic_note": "DRAM bytes of the step's 20 resident launches, from one ncu "
+                                                  "capture of a 500-MCS launch of one lattice"}),
            "clocks": clk}
     for l_ in lats:
         l_.close()
