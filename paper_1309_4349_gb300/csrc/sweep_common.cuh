@@ -10,8 +10,10 @@ struct PhaseP {
     int ntask;
 };
 
-__device__ __forceinline__ int floor_div(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
-__device__ __forceinline__ int ceil_div(int a, int b) { return -floor_div(-a, b); }
+// floor(a / 2^sh) and ceil(a / 2^sh) for any sign of a (the row spacing py of an
+// anchor sublattice is 2 or 4, so every division of the schedule is a shift).
+__device__ __forceinline__ int floor_shr(int a, int sh) { return a >> sh; }
+__device__ __forceinline__ int ceil_shr(int a, int sh) { return -((-a) >> sh); }
 
 // Phase parameters of (sweep s, phase f) and this band's share of its anchor rows.
 // Orientation 1 is (0,1) in both geometries.
@@ -35,11 +37,12 @@ __device__ void phase_params(int geometry, int Lx, int Ly, int W, int Y0, int Y1
         My = (Ly - 2) / 2 + 1;
     }
     // Anchor rows y_m = (ry + py m) mod Ly, m < My: unwrapped for m < M1.
-    const int M1 = min(My, ceil_div(Ly - ry, py));
-    const int a1 = max(ceil_div(Y0 - ry, py), 0);
-    const int b1 = min(floor_div(Y1 - 1 - ry, py), M1 - 1);
-    const int a2 = max(ceil_div(Y0 + Ly - ry, py), M1);
-    const int b2 = min(floor_div(Y1 - 1 + Ly - ry, py), My - 1);
+    const int sh = py == 4 ? 2 : 1;
+    const int M1 = min(My, ceil_shr(Ly - ry, sh));
+    const int a1 = max(ceil_shr(Y0 - ry, sh), 0);
+    const int b1 = min(floor_shr(Y1 - 1 - ry, sh), M1 - 1);
+    const int a2 = max(ceil_shr(Y0 + Ly - ry, sh), M1);
+    const int b2 = min(floor_shr(Y1 - 1 + Ly - ry, sh), My - 1);
     P->oi = oi; P->rx = rx; P->ry = ry; P->px = px; P->py = py;
     P->umax = px * (Kx - 1);
     P->a1 = a1; P->n1 = max(0, b1 - a1 + 1);
@@ -78,7 +81,8 @@ __device__ void phase_ranges(int geometry, int Lx, int Ly, int W, int lo, int hi
         Kx = (Lx - 3) / 4 + 1;
         My = (Ly - 2) / 2 + 1;
     }
-    const int M1 = min(My, ceil_div(Ly - ry, py));  // m < M1: y_m = ry + py m (no wrap)
+    const int sh = py == 4 ? 2 : 1;
+    const int M1 = min(My, ceil_shr(Ly - ry, sh));  // m < M1: y_m = ry + py m (no wrap)
     // [lo, hi) as at most two intervals of [0, Ly)
     int u[2], v[2];
     if (lo < 0) {
@@ -94,8 +98,8 @@ __device__ void phase_ranges(int geometry, int Lx, int Ly, int W, int lo, int hi
 #pragma unroll
         for (int wr = 0; wr < 2; ++wr) {
             const int off = wr ? Ly : 0;
-            int a = ceil_div(u[q] + off - ry, py);
-            int b = floor_div(v[q] - 1 + off - ry, py);
+            int a = ceil_shr(u[q] + off - ry, sh);
+            int b = floor_shr(v[q] - 1 + off - ry, sh);
             a = max(a, wr ? M1 : 0);
             b = min(b, wr ? My - 1 : M1 - 1);
             const int n = u[q] < v[q] ? max(0, b - a + 1) : 0;

@@ -283,6 +283,14 @@ __device__ __forceinline__ void helical_iteration(const uint32_t *lat, const HGe
     }
 }
 
+// Iteration f of sweep s: the colour kc in [0, 7) and the direction draw d in [0, 6)
+// (orientation d / 2, backward pair when d is odd), from the schedule's Philox block.
+__device__ __forceinline__ uint2 helical_sched(const HGeo &g, unsigned long long s, int f)
+{
+    const Philox4 w = philox4(0xFFFFFFFFu, (uint32_t)f, (uint32_t)s, (uint32_t)(s >> 32), g.k0, g.k1);
+    return make_uint2(__umulhi(w.v[0], 7u), __umulhi(w.v[1], 6u));
+}
+
 __global__ void __launch_bounds__(kHelicalThreads, 1)
 helical_resident_kernel(const SweepJob J, const SweepCall Cl)
 {
@@ -290,6 +298,7 @@ helical_resident_kernel(const SweepJob J, const SweepCall Cl)
     extern __shared__ __align__(16) uint32_t lat[];
     __shared__ uint64_t thr[16];
     __shared__ long long red[5][kWarps];
+    __shared__ uint2 sched[2];  // (colour, direction draw) of the current and the next iteration
     if (Cl.n_mcs <= 0) return;
 
     HGeo g;
@@ -317,35 +326,48 @@ helical_resident_kernel(const SweepJob J, const SweepCall Cl)
         lat[idx] = helical_word(J, y, w);
     }
     if (tid < 16) thr[tid] = J.thr[tid];
+    // Iteration f of sweep s draws its colour and direction from one Philox block;
+    // the last warp's lane 0 draws them one iteration ahead, off the tasks' path.
+    const bool sched_lane = tid == kHelicalThreads - 32;
+    if (sched_lane) sched[0] = helical_sched(g, (unsigned long long)Cl.sweep0, 0);
+    const int lx7 = g.Lx % 7;
     hcluster_sync();  // every CTA of the cluster runs before any peer writes into it
 
     const long long n_unlike0 = (tid == 0 && g.rank == 0 && Cl.trace_every > 0) ? J.state[kNUnlike] : 0;
     unsigned long long t_att = 0, t_unl = 0, t_drw = 0, t_acc = 0;
     long long t_dn = 0;
-    long long gp = 0;  // iterations done in this launch
+    int jb = 0, pb = 0;  // iteration within the block; buffer of the current schedule entry
     int block = 0;
     for (long long it = 0; it < Cl.n_mcs; ++it) {
         const long long s = Cl.sweep0 + it;
         const uint32_t s_lo = (uint32_t)(unsigned long long)s;
         const uint32_t s_hi = (uint32_t)((unsigned long long)s >> 32);
         HAcc A = {0u, 0u, 0u, 0u, 0};
-        for (int f = 0; f < 7; ++f, ++gp) {
-            const Philox4 w = philox4(0xFFFFFFFFu, (uint32_t)f, s_lo, s_hi, g.k0, g.k1);
-            const int kc = (int)__umulhi(w.v[0], 7u);
-            const int d = (int)__umulhi(w.v[1], 6u);
+        for (int f = 0; f < 7; ++f) {
+            const uint2 sc = sched[pb];
+            const int kc = (int)sc.x;
+            const int d = (int)sc.y;
             const int oi = d >> 1;
             const long long step = oi == 0 ? 1 : (oi == 1 ? g.Lx : 1 - g.Lx);
             const long long delta = (d & 1) ? step : 0;  // backward pair: its centre is anchor + o
-            const int kr = (int)((((long long)kc - delta) % 7 + 7) % 7);
-            const int jb = (int)(gp % K);
+            // kr = (kc - delta) mod 7, from delta mod 7 in {0, 1, Lx mod 7, 1 - Lx mod 7}
+            const int dm7 = (d & 1) ? (oi == 0 ? 1 : (oi == 1 ? lx7 : (lx7 <= 1 ? 1 - lx7 : 8 - lx7))) : 0;
+            int kr = kc - dm7;
+            kr += kr < 0 ? 7 : 0;
             const int e = 2 * (K - 1 - jb) + 1;
+            if (sched_lane && !(f == 6 && it + 1 == Cl.n_mcs))
+                sched[pb ^ 1] = f == 6 ? helical_sched(g, (unsigned long long)(s + 1), 0)
+                                       : helical_sched(g, (unsigned long long)s, f + 1);
             const DrawKey dk = draw_key((uint32_t)f, s_lo, s_hi, g.k0, g.k1);
             if (oi == 0) helical_iteration<0>(lat, g, kr, delta, g.D - e, g.H + 2 * e, dk, thr, A);
             else if (oi == 1) helical_iteration<1>(lat, g, kr, delta, g.D - e, g.H + 2 * e, dk, thr, A);
             else helical_iteration<2>(lat, g, kr, delta, g.D - e, g.H + 2 * e, dk, thr, A);
             __syncthreads();
+            pb ^= 1;
             const bool last = f == 6 && it + 1 == Cl.n_mcs;
-            if (jb == K - 1 && !last) {
+            const bool exch = jb == K - 1;
+            jb = exch ? 0 : jb + 1;
+            if (exch && !last) {
                 // Exchange: the D lowest and D highest band rows to the neighbours'
                 // mailboxes of parity block & 1, then this CTA's mailboxes into its
                 // halo rows, then every row's pads from the rows beside it.

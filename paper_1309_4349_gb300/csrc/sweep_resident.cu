@@ -635,15 +635,15 @@ resident_sweep_kernel(const SweepJob *__restrict__ jobs, const SweepCall *__rest
         for (int f = 0; f < 8; ++f) {
             const bool last = f == 7 && it + 1 == Cl.n_mcs;
             if (table_warp && !last) {
-                // the next phase's tables (phase 0 of the next sweep after phase 7)
-                if (f == 7) {
-                    if ((tid & 31) < 8) phase_table(J, g, K, s + 1, tid & 31, &pp[buf ^ 1][tid & 31]);
-                    __syncwarp();
-                }
+                // The next phase's task table (phase 0 of the next sweep after phase 7),
+                // then, on one lane, phase f of the next sweep: one schedule entry per
+                // phase keeps this warp's work shorter than a phase's tasks.  (Entry f
+                // of the other buffer was last read in phase f of the previous sweep.)
                 const PhaseR &Pn = f == 7 ? pp[buf ^ 1][0] : pp[buf][f + 1];
                 const TaskTab Tn = {tab_am[(f + 1) & 1], tab_row[(f + 1) & 1], kTabW, kTabRows};
                 if (blocked) build_task_table<true>(Pn, g, Tn, tid & 31, 32);
                 else build_task_table<false>(Pn, g, Tn, tid & 31, 32);
+                if ((tid & 31) == 0 && it + 1 < Cl.n_mcs) phase_table(J, g, K, s + 1, f, &pp[buf ^ 1][f]);
             }
             const PhaseR P = pp[buf][f];
             const TaskTab Tc = {tab_am[f & 1], tab_row[f & 1], kTabW, kTabRows};
