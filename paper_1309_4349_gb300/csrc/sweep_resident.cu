@@ -184,13 +184,15 @@ __device__ __forceinline__ bool table_fits(const Geo &g, const PhaseR &P, const 
 
 // Fills the table entries with index = lane0 mod step (all of them for lane0 = 0,
 // step = 1 per thread ... ), so that a warp (step 32) or a CTA (step THREADS)
-// builds it together.
-template <bool BLOCKED>
+// builds it together: the anchor masks (AM), the rows (ROWS) or both.
+template <bool BLOCKED, bool AM = true, bool ROWS = true>
 __device__ __forceinline__ void build_task_table(const PhaseR &P, const Geo &g, const TaskTab &T, int lane0,
                                                  int step)
 {
     if (!table_fits(g, P, T)) return;
-    for (int j = lane0; j < g.W; j += step) T.am[j] = anchor_mask(j << 5, P, g.Lx);
+    if (AM)
+        for (int j = lane0; j < g.W; j += step) T.am[j] = anchor_mask(j << 5, P, g.Lx);
+    if (ROWS)
     for (int mi = lane0; mi < P.c[3]; mi += step) {
         const int m = mi < P.c[0] ? P.a[0] + mi
                     : (mi < P.c[1] ? P.a[1] + mi : (mi < P.c[2] ? P.a[2] + mi : P.a[3] + mi));
@@ -605,7 +607,12 @@ resident_sweep_kernel(const SweepJob *__restrict__ jobs, const SweepCall *__rest
         lat[idx] = padded_word(J.lat, J.packing, J.pitch, y, w, g.Lx, g.W);
     }
     if (tid < 16) thr[tid] = J.thr[tid];
-    const bool table_warp = (tid >> 5) == kWarps - 1;  // builds the phase tables
+    // The last three warps prepare the next phase while the phase runs: its anchor
+    // masks, its rows, and (lane 0) one schedule entry of the next sweep.
+    const int warp = tid >> 5;
+    const bool table_warp = warp == kWarps - 1;
+    const bool row_warp = warp == kWarps - 2;
+    const bool sched_warp = warp == kWarps - 3;
     if (table_warp) {
         if ((tid & 31) < 8) phase_table(J, g, K, Cl.sweep0, tid & 31, &pp[0][tid & 31]);
         __syncwarp();
@@ -634,17 +641,23 @@ resident_sweep_kernel(const SweepJob *__restrict__ jobs, const SweepCall *__rest
         Acc A = {0u, 0u, 0u, 0u, 0};
         for (int f = 0; f < 8; ++f) {
             const bool last = f == 7 && it + 1 == Cl.n_mcs;
-            if (table_warp && !last) {
-                // The next phase's task table (phase 0 of the next sweep after phase 7),
-                // then, on one lane, phase f of the next sweep: one schedule entry per
-                // phase keeps this warp's work shorter than a phase's tasks.  (Entry f
-                // of the other buffer was last read in phase f of the previous sweep.)
-                const PhaseR &Pn = f == 7 ? pp[buf ^ 1][0] : pp[buf][f + 1];
+            if ((table_warp || row_warp) && !last) {
+                // the next phase's task table (phase 0 of the next sweep after phase 7)
+                const PhaseR Pn = f == 7 ? pp[buf ^ 1][0] : pp[buf][f + 1];
                 const TaskTab Tn = {tab_am[(f + 1) & 1], tab_row[(f + 1) & 1], kTabW, kTabRows};
-                if (blocked) build_task_table<true>(Pn, g, Tn, tid & 31, 32);
-                else build_task_table<false>(Pn, g, Tn, tid & 31, 32);
-                if ((tid & 31) == 0 && it + 1 < Cl.n_mcs) phase_table(J, g, K, s + 1, f, &pp[buf ^ 1][f]);
+                if (table_warp) {
+                    if (blocked) build_task_table<true, true, false>(Pn, g, Tn, tid & 31, 32);
+                    else build_task_table<false, true, false>(Pn, g, Tn, tid & 31, 32);
+                } else {
+                    if (blocked) build_task_table<true, false, true>(Pn, g, Tn, tid & 31, 32);
+                    else build_task_table<false, false, true>(Pn, g, Tn, tid & 31, 32);
+                }
             }
+            // Phase f of the next sweep: one schedule entry per phase.  (Entry f of the
+            // other buffer was last read in phase f of the previous sweep; phase 0's is
+            // written here before phase 7 builds its task table from it.)
+            if (sched_warp && (tid & 31) == 0 && it + 1 < Cl.n_mcs)
+                phase_table(J, g, K, s + 1, f, &pp[buf ^ 1][f]);
             const PhaseR P = pp[buf][f];
             const TaskTab Tc = {tab_am[f & 1], tab_row[f & 1], kTabW, kTabRows};
             const TaskTab *tt = &Tc;
