@@ -78,11 +78,11 @@ ISSUE_LANES_PER_SM = 128
 # 4-phase band launch of the 8192x8192 lattice; one resident helical launch of 500
 # MCS of one 402x399 lattice), valid only for the kernel sources they were taken
 # with (hash of the kernel's file + sweep_common.cuh + philox.cuh).
-TRAFFIC_C2_LAUNCH = 222208
-TRAFFIC_C3_LAUNCH = 8500736
-TRAFFIC_SOURCES = "aff7c9aafc102963"
-TRAFFIC_C6_LAUNCH = 275968
-TRAFFIC_HELICAL_SOURCES = "6a258ca347341b5c"
+TRAFFIC_C2_LAUNCH = 211200
+TRAFFIC_C3_LAUNCH = 8500480
+TRAFFIC_SOURCES = "fabfcfe5f46002be"
+TRAFFIC_C6_LAUNCH = 91392
+TRAFFIC_HELICAL_SOURCES = "6dc02bad03f1f83d"
 
 # Kernels launched per library call (fixed by the library's structure).
 LAUNCHES_SWEEP = 1

@@ -40,7 +40,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(OBJ, exist_ok=True)
     common = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
                      "-I" + os.path.join(ROOT, "include"), "-I" + CSRC]
-    common += os.environ.get("KLMC_NVCC_FLAGS", "").split()  # e.g. -DKLMC_SPEC=0 for a variant build
+    common += os.environ.get("KLMC_NVCC_FLAGS", "").split()  # e.g. -DKLMC_BAND_THREADS=512 for a variant build
 
     def compile_one(src: str) -> str:
         obj = os.path.join(OBJ, src.replace(".cu", ".o"))
