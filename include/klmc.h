@@ -126,8 +126,10 @@ klmc_status klmc_create_ex(klmc_ctx **out, const klmc_params *p);
  * "Massive Parallel Kawasaki Kinetics": one MPKK step = as many attempts as
  * sites).  Deterministic: the result depends only on seed, the lattice and the
  * absolute sweep index, not on the cluster size.  With the automatic launch shape
- * (cluster = 0) a lattice too large for one thread-block cluster's shared memory
- * runs on the tiled path: bands of rows, one CTA each, four phases per launch,
+ * (cluster = 0) a lattice of at least 786432 sites (where the tiled path measured
+ * faster) or too large for one thread-block cluster's shared memory runs on the
+ * tiled path (replicas of a batch and jobs of a server stay resident): bands of
+ * rows, one CTA each, four phases per launch,
  * rows of a bit store on 16-byte boundaries moved by bulk copies.  With an explicit
  * cluster size, EINVAL when the lattice does not fit it (each CTA's band of padded
  * bit rows plus its halo rows must fit its shared memory). */

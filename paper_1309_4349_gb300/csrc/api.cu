@@ -201,7 +201,16 @@ klmc_status ensure_clusters(klmc_ctx *c)
 
 bool tuned_shape(int Lx, int Ly, int geometry, int packing, int *cluster, int *threads);
 
-klmc_status create_one(klmc_ctx **out, const klmc_params *p, klmc_batch *owner, bool sync = true)
+// Lattices of at least this many sites run faster on the tiled path, whose bands
+// use every SM, than in one cluster's shared memory (GB300, 200 MCS of square TRI6
+// lattices: 724^2 5.7 vs 4.8 ms resident, 1024^2 5.8 vs 7.1 ms, 2048^2 6.8 vs
+// 20.1 ms); the automatic shape of a standalone handle takes it there.
+constexpr long long kTiledAutoSites = 786432;
+
+// standalone: a handle of its own (klmc_create, klmc_create_ex), which may take the
+// tiled path automatically; batch replicas and server jobs stay resident.
+klmc_status create_one(klmc_ctx **out, const klmc_params *p, klmc_batch *owner, bool sync = true,
+                       bool standalone = false)
 {
     klmc_status st = validate(p);
     if (st != KLMC_OK) return st;
@@ -229,6 +238,13 @@ klmc_status create_one(klmc_ctx **out, const klmc_params *p, klmc_batch *owner, 
         if (p->cluster == 0 &&
             resident_smem_bytes(p->Lx, p->Ly, c->cluster) > (size_t)resident_max_smem_bytes())
             c->cluster = -1;  // automatic choice, too large for shared memory: tiled path
+        if (standalone && p->cluster == 0 && c->cluster > 0 && c->N >= kTiledAutoSites) {
+            int dev = 0, sms = 0;
+            if (cudaGetDevice(&dev) == cudaSuccess &&
+                cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+                tiled_plan(p->Lx, p->Ly, sms).K >= 2)
+                c->cluster = -1;  // automatic choice, large: bands over every SM
+        }
         c->threads = resident_default_threads(c->cluster);
         if (p->cluster == 0 && p->threads == 0)
             tuned_shape(p->Lx, p->Ly, p->geometry, c->p.packing, &c->cluster, &c->threads);
@@ -649,13 +665,13 @@ klmc_status klmc_create(klmc_ctx **out, int32_t L, double composition_A, double 
     p.fraction_A = composition_A;
     p.omega_over_kT = omega_over_kT;
     p.seed = seed;
-    return create_one(out, &p, nullptr);
+    return create_one(out, &p, nullptr, true, true);
 }
 
 klmc_status klmc_create_ex(klmc_ctx **out, const klmc_params *p)
 {
     if (!out) return fail(KLMC_EINVAL, "out is NULL");
-    return create_one(out, p, nullptr);
+    return create_one(out, p, nullptr, true, true);
 }
 
 klmc_status klmc_sweep(klmc_ctx *c, int64_t n_mcs) { return sweep_one(c, n_mcs, 0, nullptr); }

@@ -639,3 +639,25 @@ def test_c2_one_run_2000_mcs_all_histograms():
         _hist_equal(lat, t, 1)
     assert_same_run(lat, r)
     lat.close()
+
+
+def test_large_standalone_lattice_takes_tiled_path_automatically():
+    """A standalone 1024 x 1000 lattice (at least 786432 sites) with the automatic
+    shape runs on the tiled path, exactly; the same lattice as a batch replica stays
+    resident and gives the same lattice."""
+    Lx, Ly, nA, bw, seed = 1024, 1000, 307200, 0.7, 31
+    lat = make(Lx, Ly, nA, bw, seed)
+    b = klmc.Batch([dict(Lx=Lx, Ly=Ly, n_A=nA, omega_over_kT=bw, seed=seed)])
+    try:
+        assert lat.launch_shape()[0] == -1
+        lat.sweep(2)
+        b.sweep(2)
+        assert b.launch_shape(0)[0] >= 1
+        ref = oracle.run(Lx, Ly, oracle.TRI6, bw, seed, oracle.init(Lx, Ly, nA, seed), 0, 2)
+        assert np.array_equal(lat.get_lattice(), ref.lattice)
+        assert np.array_equal(b.replicas[0].get_lattice(), ref.lattice)
+        c = lat.counters()
+        assert (c["attempts"], c["draws"], c["accepts"]) == (ref.attempts, ref.draws, ref.accepts)
+    finally:
+        b.close()
+        lat.close()
