@@ -290,13 +290,29 @@ klmc_status klmc_get_shape(klmc_ctx *c, int32_t *Lx, int32_t *Ly, int32_t *geome
 /* Autotuner: picks the fastest launch shape for this lattice's size by timing
  * every valid shape -- 1, 2, 4, 8 or 16 CTAs per lattice with 512, 256 or 128
  * threads per CTA, and the tiled per-phase path -- for probe_sweeps sweeps
- * on a scratch copy of the lattice at its current sweep index.  Every candidate's
- * resulting lattice and counters must equal the first candidate's (exactness
- * gate; a differing shape is an error, KLMC_ESTATE).  The choice is cached per
- * (Lx, Ly, geometry, packing) for the process and applied to the handle; the
- * lattice, counters and trajectory are unchanged.  Synchronises.  Either output
- * pointer may be NULL.  ESTATE for a replica view. */
+ * on a scratch copy of the lattice at its current sweep index; for a handle
+ * created with packing KLMC_PACK_AUTO, every shape with each store format (1 bit
+ * and 1 byte per site), the handle's store then moved to the faster one (see
+ * klmc_get_packing).  Every candidate's resulting sites and counters must equal
+ * the first candidate's (exactness gate; a differing candidate is an error,
+ * KLMC_ESTATE).  The choice is cached per (Lx, Ly, geometry, packing, with AUTO
+ * its own key) for the process, applied to the handle and to handles of that
+ * size created later with the automatic shape; the lattice, counters and
+ * trajectory are unchanged.  Synchronises.  Either output pointer may be NULL.
+ * ESTATE for a replica view; ENOMEM when the scratch copies cannot be allocated. */
 klmc_status klmc_autotune(klmc_ctx *c, int32_t probe_sweeps, int32_t *cluster, int32_t *threads);
+
+/* Moves the handle's lattice into a device store of the given format
+ * (KLMC_PACK_BIT: 1 bit per site in 32-bit words; KLMC_PACK_BYTE: 1 byte per
+ * site), leaving its sites, counters and sweep index as they are; the old store
+ * is freed and a device pointer to it is no longer valid.  Enqueued on the
+ * handle's stream (synchronises only with a caller's allocator, before freeing).
+ * EINVAL for another value, ESTATE for a replica view, ENOMEM when the new store
+ * cannot be allocated (the handle is then unchanged). */
+klmc_status klmc_set_packing(klmc_ctx *c, int32_t packing);
+
+/* Current store format of the handle: KLMC_PACK_BIT or KLMC_PACK_BYTE. */
+klmc_status klmc_get_packing(klmc_ctx *c, int32_t *packing);
 
 /* Launch shape of the handle's sweep: CTAs per lattice (thread-block cluster
  * size, -1 for the tiled per-phase path) and threads per CTA.  Either pointer may

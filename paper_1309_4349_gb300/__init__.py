@@ -117,6 +117,8 @@ def lib():
         "klmc_set_lattice_device": [vp, vp, i64, i64],
         "klmc_get_shape": [vp, P(i32), P(i32), P(i32), P(i64)],
         "klmc_get_launch": [vp, P(i32), P(i32)],
+        "klmc_set_packing": [vp, i32],
+        "klmc_get_packing": [vp, P(i32)],
         "klmc_autotune": [vp, i32, P(i32), P(i32)],
         "klmc_synchronize": [vp],
         "klmc_destroy": [vp],
@@ -380,6 +382,16 @@ class Lattice:
         c, t = ctypes.c_int32(), ctypes.c_int32()
         _check(lib().klmc_get_launch(self._h, ctypes.byref(c), ctypes.byref(t)))
         return c.value, t.value
+
+    def packing(self) -> int:
+        """Store format of the device lattice: PACK_BIT or PACK_BYTE (klmc_get_packing)."""
+        v = ctypes.c_int32()
+        _check(lib().klmc_get_packing(self._h, ctypes.byref(v)))
+        return v.value
+
+    def set_packing(self, packing: int) -> None:
+        """Moves the device lattice into a store of the given format (klmc_set_packing)."""
+        _check(lib().klmc_set_packing(self._h, int(packing)))
 
     def plan(self) -> int:
         """Phases advanced between halo exchanges of the resident sweep (1: every phase)."""

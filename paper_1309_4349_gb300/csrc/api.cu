@@ -96,6 +96,36 @@ void free_all(klmc_ctx *c)
     cudaStreamSynchronize(c->stream);
 }
 
+// Returns one allocation of dev_alloc; with a caller's allocator after the stream's
+// work is done (its frees need not be stream-ordered).
+void dev_free(klmc_ctx *c, void *p)
+{
+    for (size_t i = 0; i < c->allocs.size(); ++i) {
+        if (c->allocs[i].first != p) continue;
+        if (c->p.alloc && c->p.free) {
+            cudaStreamSynchronize(c->stream);
+            c->p.free(p, c->allocs[i].second, c->p.stream, c->p.user);
+        } else if (!c->p.alloc) {
+            cudaFreeAsync(p, c->stream);
+        }
+        c->allocs.erase(c->allocs.begin() + (long)i);
+        return;
+    }
+}
+
+// Row pitch and size of a device store: rows of 16 bytes, of 32-bit words (a bit
+// per site) or of bytes (a byte per site).
+void store_layout(int Lx, int Ly, int packing, int *pitch, size_t *bytes)
+{
+    if (packing == KLMC_PACK_BIT) {
+        *pitch = ((Lx + 31) / 32 + 3) / 4 * 4;
+        *bytes = (size_t)*pitch * 4 * (size_t)Ly;
+    } else {
+        *pitch = (Lx + 15) / 16 * 16;
+        *bytes = (size_t)*pitch * (size_t)Ly;
+    }
+}
+
 klmc_status validate(const klmc_params *p)
 {
     if (!p) return fail(KLMC_EINVAL, "params is NULL");
@@ -199,7 +229,7 @@ klmc_status ensure_clusters(klmc_ctx *c)
     return KLMC_OK;
 }
 
-bool tuned_shape(int Lx, int Ly, int geometry, int packing, int *cluster, int *threads);
+bool tuned_shape(int Lx, int Ly, int geometry, int packing, int *cluster, int *threads, int *tuned_packing);
 
 // Lattices of at least this many sites run faster on the tiled path, whose bands
 // use every SM, than in one cluster's shared memory (GB300, 200 MCS of square TRI6
@@ -219,6 +249,7 @@ klmc_status create_one(klmc_ctx **out, const klmc_params *p, klmc_batch *owner, 
     klmc_ctx *c = new (std::nothrow) klmc_ctx();
     if (!c) return fail(KLMC_ENOMEM, "host allocation failed");
     c->p = *p;
+    c->auto_packing = p->packing == KLMC_PACK_AUTO && p->boundary != KLMC_HELICAL;
     if (c->p.packing == KLMC_PACK_AUTO) c->p.packing = KLMC_PACK_BIT;
     c->owner = owner;
     c->stream = (cudaStream_t)p->stream;
@@ -246,18 +277,15 @@ klmc_status create_one(klmc_ctx **out, const klmc_params *p, klmc_batch *owner, 
                 c->cluster = -1;  // automatic choice, large: bands over every SM
         }
         c->threads = resident_default_threads(c->cluster);
-        if (p->cluster == 0 && p->threads == 0)
-            tuned_shape(p->Lx, p->Ly, p->geometry, c->p.packing, &c->cluster, &c->threads);
+        int tuned_packing = c->p.packing;
+        if (p->cluster == 0 && p->threads == 0 &&
+            tuned_shape(p->Lx, p->Ly, p->geometry, c->auto_packing ? KLMC_PACK_AUTO : c->p.packing, &c->cluster,
+                        &c->threads, &tuned_packing))
+            c->p.packing = tuned_packing;  // the autotuner's store format for this size
         c->auto_shape = p->cluster == 0 && p->threads == 0;
         if (p->threads != 0) c->threads = p->threads;
     }
-    if (c->p.packing == KLMC_PACK_BIT) {
-        c->pitch = (c->W + 3) / 4 * 4;  // 16-byte rows
-        c->lat_bytes = (size_t)c->pitch * 4 * p->Ly;
-    } else {
-        c->pitch = (p->Lx + 15) / 16 * 16;
-        c->lat_bytes = (size_t)c->pitch * p->Ly;
-    }
+    store_layout(p->Lx, p->Ly, c->p.packing, &c->pitch, &c->lat_bytes);
     c->lat = dev_alloc(c, c->lat_bytes);
     c->state = (long long *)dev_alloc(c, kStateSlots * sizeof(long long));
     c->init_scratch = dev_alloc(c, init_scratch_bytes());
@@ -452,7 +480,7 @@ klmc_status sweep_one(klmc_ctx *c, int64_t n_mcs, int64_t trace_every, int64_t *
 // with every candidate's result required to be identical.
 // ---------------------------------------------------------------------------
 struct TuneKey {
-    int Lx, Ly, geometry, packing;
+    int Lx, Ly, geometry, packing;  // packing KLMC_PACK_AUTO: the tuner also picks the store format
     bool operator<(const TuneKey &o) const
     {
         if (Lx != o.Lx) return Lx < o.Lx;
@@ -461,39 +489,82 @@ struct TuneKey {
         return packing < o.packing;
     }
 };
+struct Tuned {
+    int cluster, threads, packing;
+};
 std::mutex g_tune_mutex;
-std::map<TuneKey, std::pair<int, int>> g_tune_cache;
+std::map<TuneKey, Tuned> g_tune_cache;
 
-bool tuned_shape(int Lx, int Ly, int geometry, int packing, int *cluster, int *threads)
+bool tuned_shape(int Lx, int Ly, int geometry, int packing, int *cluster, int *threads, int *tuned_packing)
 {
     std::lock_guard<std::mutex> lock(g_tune_mutex);
     auto it = g_tune_cache.find(TuneKey{Lx, Ly, geometry, packing});
     if (it == g_tune_cache.end()) return false;
-    *cluster = it->second.first;
-    *threads = it->second.second;
+    *cluster = it->second.cluster;
+    *threads = it->second.threads;
+    *tuned_packing = it->second.packing;
     return true;
 }
 
+// Moves the handle's lattice into a store of the other format (its sites, counters
+// and sweep index unchanged).  Graphs and the tiled path's second buffer, which
+// hold the old store's address or size, are dropped and rebuilt on next use.
+klmc_status convert_store(klmc_ctx *c, int packing)
+{
+    if (packing == c->job.packing) return KLMC_OK;
+    klmc_status st = ensure_bytes(c);
+    if (st != KLMC_OK) return st;
+    int pitch = 0;
+    size_t bytes = 0;
+    store_layout(c->p.Lx, c->p.Ly, packing, &pitch, &bytes);
+    void *lat = dev_alloc(c, bytes);
+    if (!lat) return fail(KLMC_ENOMEM, "device allocation of the new store failed");
+    KLMC_CUDA(launch_unpack(c->lat, c->job.packing, c->p.Lx, c->p.Ly, c->pitch, c->dbytes, c->stream));
+    KLMC_CUDA(cudaMemsetAsync(lat, 0, bytes, c->stream));  // row padding stays zero
+    KLMC_CUDA(launch_pack(c->dbytes, lat, packing, c->p.Lx, c->p.Ly, pitch, c->stream));
+    for (auto &g : c->graphs) cudaGraphExecDestroy(g.second);
+    c->graphs.clear();
+    if (c->tiled_alt) dev_free(c, c->tiled_alt);
+    c->tiled_alt = nullptr;
+    c->tiled = TiledPlan{0, 0, 0, 0};
+    dev_free(c, c->lat);
+    c->lat = lat;
+    c->lat_bytes = bytes;
+    c->pitch = pitch;
+    c->p.packing = packing;
+    c->job.lat = lat;
+    c->job.pitch = pitch;
+    c->job.packing = packing;
+    return KLMC_OK;
+}
+
+// A store for the probes: the lattice at its start, its format, and (for the tiled
+// path's blocks) a second buffer of its size.
+struct ProbeStore {
+    const void *src;
+    size_t bytes;
+    int packing, pitch;
+    void *alt;
+};
+
 struct ProbeResult {
     float ms;
-    std::vector<uint8_t> lattice;
+    std::vector<uint8_t> sites;  // one byte per site after the probe
     long long state[kStateSlots];
 };
 
-// Runs n sweeps of the handle's lattice with launch shape (cluster, threads) on the
-// scratch lattice/state (copied from the handle first).
-klmc_status probe_shape(klmc_ctx *c, void *scratch_lat, long long *scratch_state, int cluster,
-                        int threads, int n, cudaEvent_t e0, cudaEvent_t e1, ProbeResult *out)
+// Runs n sweeps of the lattice in store `ps` with launch shape (cluster, threads) on
+// the scratch lattice/state (copied from the store and the handle first).
+klmc_status probe_shape(klmc_ctx *c, const ProbeStore &ps, void *scratch_lat, long long *scratch_state,
+                        int cluster, int threads, int n, cudaEvent_t e0, cudaEvent_t e1, ProbeResult *out)
 {
     SweepJob J = c->job;
     J.lat = scratch_lat;
     J.state = scratch_state;
-    if (cluster < 0) {
-        klmc_status st = ensure_tiled(c);
-        if (st != KLMC_OK) return st;
-    }
+    J.packing = ps.packing;
+    J.pitch = ps.pitch;
     for (int rep = 0; rep < 2; ++rep) {  // the first run warms up; the second is timed
-        KLMC_CUDA(cudaMemcpyAsync(scratch_lat, c->lat, c->lat_bytes, cudaMemcpyDeviceToDevice, c->stream));
+        KLMC_CUDA(cudaMemcpyAsync(scratch_lat, ps.src, ps.bytes, cudaMemcpyDeviceToDevice, c->stream));
         KLMC_CUDA(cudaMemcpyAsync(scratch_state, c->state, kStateSlots * sizeof(long long),
                                   cudaMemcpyDeviceToDevice, c->stream));
         const long long base = c->sweep;
@@ -501,7 +572,7 @@ klmc_status probe_shape(klmc_ctx *c, void *scratch_lat, long long *scratch_state
                                   cudaMemcpyHostToDevice, c->stream));
         KLMC_CUDA(cudaEventRecord(e0, c->stream));
         if (cluster < 0) {
-            KLMC_CUDA(path_sweeps(c, J, 0, n, c->stream));
+            KLMC_CUDA(launch_tiled_phases(J, c->tiled, ps.alt, ps.bytes, 0, n, c->stream));
             KLMC_CUDA(launch_advance(scratch_state, n, c->stream));
         } else {
             SweepCall call;
@@ -517,68 +588,123 @@ klmc_status probe_shape(klmc_ctx *c, void *scratch_lat, long long *scratch_state
         KLMC_CUDA(cudaEventSynchronize(e1));
     }
     KLMC_CUDA(cudaEventElapsedTime(&out->ms, e0, e1));
-    out->lattice.resize(c->lat_bytes);
-    KLMC_CUDA(cudaMemcpy(out->lattice.data(), scratch_lat, c->lat_bytes, cudaMemcpyDeviceToHost));
-    KLMC_CUDA(cudaMemcpy(out->state, scratch_state, sizeof(out->state), cudaMemcpyDeviceToHost));
+    KLMC_CUDA(launch_unpack(scratch_lat, ps.packing, c->p.Lx, c->p.Ly, ps.pitch, c->dbytes, c->stream));
+    out->sites.resize((size_t)c->N);
+    KLMC_CUDA(cudaMemcpyAsync(out->sites.data(), c->dbytes, (size_t)c->N, cudaMemcpyDeviceToHost, c->stream));
+    KLMC_CUDA(cudaMemcpyAsync(out->state, scratch_state, sizeof(out->state), cudaMemcpyDeviceToHost, c->stream));
+    KLMC_CUDA(cudaStreamSynchronize(c->stream));
     return KLMC_OK;
 }
 
+// Times every valid launch shape -- and, for a handle whose store format is the
+// library's choice, both formats -- and keeps the fastest; every candidate must
+// leave the same sites and counters as the first.
 klmc_status autotune(klmc_ctx *c, int probe_sweeps)
 {
     if (c->helical) return KLMC_OK;  // one launch shape: the iteration launches
-    const TuneKey key{c->p.Lx, c->p.Ly, c->p.geometry, c->job.packing};
+    const TuneKey key{c->p.Lx, c->p.Ly, c->p.geometry, c->auto_packing ? (int)KLMC_PACK_AUTO : c->job.packing};
     {
-        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        std::unique_lock<std::mutex> lock(g_tune_mutex);
         auto it = g_tune_cache.find(key);
         if (it != g_tune_cache.end()) {
-            c->cluster = it->second.first;
-            c->threads = it->second.second;
-            return KLMC_OK;
+            const Tuned t = it->second;
+            lock.unlock();
+            c->cluster = t.cluster;
+            c->threads = t.threads;
+            return convert_store(c, t.packing);
         }
     }
-    std::vector<std::pair<int, int>> cands;
+    std::vector<std::pair<int, int>> shapes;
     for (int C : {1, 2, 4, 8, 16}) {
         if (C > 1 && c->p.Ly / C < 4) continue;
         if (resident_smem_bytes(c->p.Lx, c->p.Ly, C) > (size_t)resident_max_smem_bytes()) continue;
-        cands.push_back({C, 512});
-        cands.push_back({C, 256});
-        cands.push_back({C, 128});
+        shapes.push_back({C, 512});
+        shapes.push_back({C, 256});
+        shapes.push_back({C, 128});
     }
-    cands.push_back({-1, 256});
-    void *slat = dev_alloc(c, c->lat_bytes);
+    shapes.push_back({-1, 256});
+    klmc_status st = ensure_bytes(c);
+    if (st == KLMC_OK) st = ensure_tiled(c);
+    if (st != KLMC_OK) return st;
+    std::vector<ProbeStore> stores{{c->lat, c->lat_bytes, c->job.packing, c->pitch, c->tiled_alt}};
+    std::vector<void *> scratch;  // freed on every return below
+    auto release = [&]() {
+        for (void *q : scratch) dev_free(c, q);
+        scratch.clear();
+    };
+    size_t max_bytes = c->lat_bytes;
+    if (c->auto_packing) {  // the other format's copy of the lattice
+        ProbeStore o{};
+        o.packing = c->job.packing == KLMC_PACK_BIT ? KLMC_PACK_BYTE : KLMC_PACK_BIT;
+        store_layout(c->p.Lx, c->p.Ly, o.packing, &o.pitch, &o.bytes);
+        void *lat = dev_alloc(c, o.bytes);
+        if (lat) scratch.push_back(lat);
+        void *alt = c->tiled.K >= 2 ? dev_alloc(c, o.bytes) : nullptr;
+        if (alt) scratch.push_back(alt);
+        if (!lat || (c->tiled.K >= 2 && !alt)) {
+            release();
+            return fail(KLMC_ENOMEM, "autotune scratch allocation failed");
+        }
+        cudaError_t e = launch_unpack(c->lat, c->job.packing, c->p.Lx, c->p.Ly, c->pitch, c->dbytes, c->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(lat, 0, o.bytes, c->stream);
+        if (e == cudaSuccess) e = launch_pack(c->dbytes, lat, o.packing, c->p.Lx, c->p.Ly, o.pitch, c->stream);
+        if (e != cudaSuccess) {
+            release();
+            return fail(KLMC_ECUDA, std::string("autotune: ") + cudaGetErrorString(e));
+        }
+        o.src = lat;
+        o.alt = alt;
+        stores.push_back(o);
+        max_bytes = std::max(max_bytes, o.bytes);
+    }
+    void *slat = dev_alloc(c, max_bytes);
+    if (slat) scratch.push_back(slat);
     long long *sstate = (long long *)dev_alloc(c, kStateSlots * sizeof(long long));
-    if (!slat || !sstate) return fail(KLMC_ENOMEM, "autotune scratch allocation failed");
+    if (sstate) scratch.push_back(sstate);
+    if (!slat || !sstate) {
+        release();
+        return fail(KLMC_ENOMEM, "autotune scratch allocation failed");
+    }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
-    KLMC_CUDA(cudaEventCreate(&e0));
-    KLMC_CUDA(cudaEventCreate(&e1));
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        release();
+        return fail(KLMC_ECUDA, "autotune: event creation failed");
+    }
     ProbeResult ref, cur;
     float best_ms = 0.f;
-    std::pair<int, int> best = cands.front();
-    klmc_status st = KLMC_OK;
-    for (size_t i = 0; i < cands.size() && st == KLMC_OK; ++i) {
-        ProbeResult &r = i == 0 ? ref : cur;
-        st = probe_shape(c, slat, sstate, cands[i].first, cands[i].second, probe_sweeps, e0, e1, &r);
-        if (st != KLMC_OK) break;
-        if (i > 0) {
-            bool same = r.lattice == ref.lattice;
-            for (int k = kNUnlike; k <= kAccepts; ++k) same = same && r.state[k] == ref.state[k];
-            if (!same) {
-                st = fail(KLMC_ESTATE, "autotune: launch shape (" + std::to_string(cands[i].first) + ", " +
-                                           std::to_string(cands[i].second) +
-                                           ") changed the result; refusing it");
-                break;
+    Tuned best{shapes.front().first, shapes.front().second, c->job.packing};
+    bool first = true;
+    for (const ProbeStore &ps : stores) {
+        for (size_t i = 0; i < shapes.size() && st == KLMC_OK; ++i) {
+            ProbeResult &r = first ? ref : cur;
+            st = probe_shape(c, ps, slat, sstate, shapes[i].first, shapes[i].second, probe_sweeps, e0, e1, &r);
+            if (st != KLMC_OK) break;
+            if (!first) {
+                bool same = r.sites == ref.sites;
+                for (int k = kNUnlike; k <= kAccepts; ++k) same = same && r.state[k] == ref.state[k];
+                if (!same) {
+                    st = fail(KLMC_ESTATE, "autotune: launch shape (" + std::to_string(shapes[i].first) + ", " +
+                                               std::to_string(shapes[i].second) + ") with store format " +
+                                               std::to_string(ps.packing) + " changed the result; refusing it");
+                    break;
+                }
             }
-        }
-        if (i == 0 || r.ms < best_ms) {
-            best_ms = r.ms;
-            best = cands[i];
+            if (first || r.ms < best_ms) {
+                best_ms = r.ms;
+                best = Tuned{shapes[i].first, shapes[i].second, ps.packing};
+            }
+            first = false;
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    release();
     if (st != KLMC_OK) return st;
-    c->cluster = best.first;
-    c->threads = best.second;
+    c->cluster = best.cluster;
+    c->threads = best.threads;
+    st = convert_store(c, best.packing);
+    if (st != KLMC_OK) return st;
     std::lock_guard<std::mutex> lock(g_tune_mutex);
     g_tune_cache[key] = best;
     return KLMC_OK;
@@ -956,6 +1082,22 @@ klmc_status klmc_autotune(klmc_ctx *c, int32_t probe_sweeps, int32_t *cluster, i
     if (st != KLMC_OK) return st;
     if (cluster) *cluster = c->cluster;
     if (threads) *threads = c->threads;
+    return KLMC_OK;
+}
+
+klmc_status klmc_set_packing(klmc_ctx *c, int32_t packing)
+{
+    if (!c) return fail(KLMC_EINVAL, "ctx is NULL");
+    if (packing != KLMC_PACK_BIT && packing != KLMC_PACK_BYTE)
+        return fail(KLMC_EINVAL, "packing must be KLMC_PACK_BIT or KLMC_PACK_BYTE");
+    if (c->owner) return fail(KLMC_ESTATE, "a replica view's store belongs to its batch");
+    return convert_store(c, packing);
+}
+
+klmc_status klmc_get_packing(klmc_ctx *c, int32_t *packing)
+{
+    if (!c || !packing) return fail(KLMC_EINVAL, "NULL argument");
+    *packing = c->job.packing;
     return KLMC_OK;
 }
 

@@ -19,6 +19,7 @@ struct klmc_ctx {
     int cluster = 1;              // CTAs per lattice in the resident sweep (-1: tiled path)
     int threads = 512;            // threads per CTA of the resident sweep (128, 256 or 512)
     bool auto_shape = true;       // shape chosen by the library (params cluster = threads = 0)
+    bool auto_packing = false;    // store format chosen by the library (params packing = AUTO)
     bool helical = false;         // helical boundary, seven-colour schedule (sweep_mpkk.cu)
     size_t lat_bytes = 0;
     void *lat = nullptr;
