@@ -466,7 +466,7 @@ def test_large_lattice_on_full_cluster():
     """2048 x 2048 split over 16 CTAs (the largest side of the serving workload)."""
     Lx = Ly = 2048
     nA = Lx * Ly * 3 // 10
-    lat = make(Lx, Ly, nA, 0.7, 9)
+    lat = make(Lx, Ly, nA, 0.7, 9, cluster=16)
     assert lat.launch_shape()[0] == 16
     lat.sweep(1)
     ref = oracle.run(Lx, Ly, klmc.TRI6, 0.7, 9, oracle.init(Lx, Ly, nA, 9), 0, 1)
