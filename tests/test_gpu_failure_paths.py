@@ -172,3 +172,35 @@ def test_server_job_enomem_fails_only_that_job():
         assert np.array_equal(srv.lattice(jid, 48 * 40), ref.lattice)
         assert r["n_unlike"] == ref.n_unlike
     srv.close()
+
+
+def test_store_conversion_enomem_leaves_handle_unchanged():
+    """klmc_set_packing and the autotuner's store-format probes allocate new stores:
+    refused, they report ENOMEM, hold nothing more and leave the handle's store as
+    it was; granted, the old store is returned to the allocator."""
+    fa = FailingAllocator()
+    st, h = create(fa, packing=klmc.PACK_AUTO)
+    assert st == 0
+    lat = klmc.Lattice(0, _handle=h)
+    lat.sweep(2)
+    before = lat.get_lattice()
+    held = dict(fa.outstanding)
+    fa.refuse = True
+    with pytest.raises(klmc.KlmcError) as e:
+        lat.set_packing(klmc.PACK_BYTE)
+    assert e.value.status == ENOMEM
+    with pytest.raises(klmc.KlmcError) as e:
+        lat.autotune(1)
+    assert e.value.status == ENOMEM
+    assert fa.outstanding == held
+    assert lat.packing() == klmc.PACK_BIT
+    fa.refuse = False
+    lat.set_packing(klmc.PACK_BYTE)
+    assert np.array_equal(lat.get_lattice(), before)
+    assert len(fa.outstanding) == len(held)  # the bit store went back, the byte store came in
+    assert sum(fa.outstanding.values()) > sum(held.values())
+    lat.sweep(2)
+    ref = oracle.run(64, 48, klmc.TRI6, 0.7, 11, oracle.init(64, 48, 64 * 48 // 3, 11), 0, 4)
+    assert np.array_equal(lat.get_lattice(), ref.lattice)
+    lat.close()
+    assert not fa.outstanding
