@@ -236,9 +236,10 @@ __device__ __forceinline__ void helical_iteration(const uint32_t *lat, const HGe
         int y = g.Y0 - g.D + lr;
         y = y < 0 ? y + g.Ly : (y >= g.Ly ? y - g.Ly : y);
         const int x0 = j << 5;
-        const long long a0 = (long long)y * g.Lx + x0;  // site index of position 0 of the word
+        const uint32_t a0 = (uint32_t)y * (uint32_t)g.Lx + (uint32_t)x0;  // site of position 0 (< N < 2^31)
         // anchors: positions p with (a0 + p) = kr mod 7, below Lx
-        const int o = (int)(((long long)kr - a0 % 7 + 14) % 7);
+        int o = kr - (int)(a0 % 7u);
+        o += o < 0 ? 7 : 0;
         uint32_t am = 0x10204081u << o;  // bits o, o+7, o+14, o+21, o+28
         if (g.Lx - x0 < 32) am &= (1u << (g.Lx - x0)) - 1u;
         uint32_t ta, tb;
@@ -247,7 +248,7 @@ __device__ __forceinline__ void helical_iteration(const uint32_t *lat, const HGe
         const uint32_t unl = (ta ^ tb) & am;
         const uint32_t dmask = unl & draw_positions<kTRI6>(S, g.sign);
         uint32_t acc = unl & ~dmask;
-        acc |= helical_draws(dmask, S, a0 + delta, g.N, dk, thr);
+        acc |= helical_draws(dmask, S, (long long)a0 + delta, g.N, dk, thr);
         const bool own = (unsigned)(lr - g.D) < (unsigned)g.H;
         if (own) {
             A.att += __popc(am);
