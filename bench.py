@@ -81,8 +81,8 @@ ISSUE_LANES_PER_SM = 128
 TRAFFIC_C2_LAUNCH = 211200
 TRAFFIC_C3_LAUNCH = 8500480
 TRAFFIC_SOURCES = "fabfcfe5f46002be"
-TRAFFIC_C6_LAUNCH = 91392
-TRAFFIC_HELICAL_SOURCES = "6dc02bad03f1f83d"
+TRAFFIC_C6_LAUNCH = 90624
+TRAFFIC_HELICAL_SOURCES = "4e4cb06710757526"
 
 # Kernels launched per library call (fixed by the library's structure).
 LAUNCHES_SWEEP = 1

@@ -192,8 +192,10 @@ struct HAcc {
 };
 
 // Accept bits of the positions in dmask; the draw of position p uses the counter
-// of site (base + p) mod N.
-__device__ __forceinline__ uint32_t helical_draws(uint32_t dmask, const Planes &S, long long base, long long N,
+// of site (base + p) mod N.  32-bit arithmetic: a lattice resident in one
+// cluster's shared memory has far fewer than 2^30 sites, and base lies within
+// [-Lx, N + Lx).
+__device__ __forceinline__ uint32_t helical_draws(uint32_t dmask, const Planes &S, int base, int N,
                                                   const DrawKey &dk, const uint64_t *thr)
 {
     uint32_t acc = 0u;
@@ -203,9 +205,9 @@ __device__ __forceinline__ uint32_t helical_draws(uint32_t dmask, const Planes &
         dm &= dm - 1u;
         const int p2 = dm != 0u ? __ffs(dm) - 1 : p1;  // an odd last draw is repeated
         dm &= dm - 1u;
-        long long c1 = base + p1, c2 = base + p2;
-        c1 = c1 >= N ? c1 - N : (c1 < 0 ? c1 + N : c1);
-        c2 = c2 >= N ? c2 - N : (c2 < 0 ? c2 + N : c2);
+        int c1 = base + p1, c2 = base + p2;
+        c1 += c1 >= N ? -N : (c1 < 0 ? N : 0);
+        c2 += c2 >= N ? -N : (c2 < 0 ? N : 0);
         uint32_t r1, r2;
         philox2_w0_key((uint32_t)c1, (uint32_t)c2, dk, r1, r2);
         const uint32_t S1 = ((S.s0 >> p1) & 1u) | (((S.s1 >> p1) & 1u) << 1) | (((S.s2 >> p1) & 1u) << 2) |
@@ -221,7 +223,7 @@ __device__ __forceinline__ uint32_t helical_draws(uint32_t dmask, const Planes &
 // One iteration: anchors of residue kr mod 7 in local rows [lr0, lr0 + nrows),
 // orientation OI, draw counters shifted by delta (the centre of a backward pair).
 template <int OI>
-__device__ __forceinline__ void helical_iteration(const uint32_t *lat, const HGeo &g, int kr, long long delta,
+__device__ __forceinline__ void helical_iteration(const uint32_t *lat, const HGeo &g, int kr, int delta,
                                                   int lr0, int nrows, const DrawKey &dk, const uint64_t *thr,
                                                   HAcc &A)
 {
@@ -248,7 +250,7 @@ __device__ __forceinline__ void helical_iteration(const uint32_t *lat, const HGe
         const uint32_t unl = (ta ^ tb) & am;
         const uint32_t dmask = unl & draw_positions<kTRI6>(S, g.sign);
         uint32_t acc = unl & ~dmask;
-        acc |= helical_draws(dmask, S, (long long)a0 + delta, g.N, dk, thr);
+        acc |= helical_draws(dmask, S, (int)a0 + delta, (int)g.N, dk, thr);
         const bool own = (unsigned)(lr - g.D) < (unsigned)g.H;
         if (own) {
             A.att += __popc(am);
@@ -350,7 +352,7 @@ helical_resident_kernel(const SweepJob J, const SweepCall Cl)
             const int d = (int)sc.y;
             const int oi = d >> 1;
             const long long step = oi == 0 ? 1 : (oi == 1 ? g.Lx : 1 - g.Lx);
-            const long long delta = (d & 1) ? step : 0;  // backward pair: its centre is anchor + o
+            const int delta = (d & 1) ? (int)step : 0;  // backward pair: its centre is anchor + o
             // kr = (kc - delta) mod 7, from delta mod 7 in {0, 1, Lx mod 7, 1 - Lx mod 7}
             const int dm7 = (d & 1) ? (oi == 0 ? 1 : (oi == 1 ? lx7 : (lx7 <= 1 ? 1 - lx7 : 8 - lx7))) : 0;
             int kr = kc - dm7;
