@@ -95,12 +95,14 @@ C3 = dict(L=8192, omega=0.85, seed=7, mcs=1000, trace_every=10)
 C4 = dict(n=256, L_min=100, L_max=1024, f_min=0.1, f_max=0.5, w_min=0.1, w_max=1.2, mcs=5000,
           seed0=1000, draw_seed=20260)
 # Serving: the arrival rate offers 0.8 of the server's measured capacity on this
-# job mix (C5_CAPACITY attempts/s); the configuration's 10000 jobs take about
-# 10000 x 1.3e10 / (0.8 x C5_CAPACITY) seconds to arrive, so the default run
-# serves the first C5_JOBS of the stream (--c5-jobs 10000 for all of them).
+# job mix (C5_CAPACITY attempts/s: the first 1000 jobs of the stream submitted at
+# once, `--workload c5 --rate 1000000`, served at 2.41e11 attempts/s on GB300);
+# the configuration's 10000 jobs take about 10000 x 1.3e10 / (0.8 x C5_CAPACITY)
+# seconds to arrive, so the default run serves the first C5_JOBS of the stream
+# (--c5-jobs 10000 for all of them).
 C5 = dict(L_min=64, L_max=2048, f_min=0.1, f_max=0.5, w_min=0.1, w_max=1.2, mcs_min=1e3, mcs_max=1e5,
           seed0=1000000, draw_seed=77, budget=16 << 30)
-C5_CAPACITY = 1.5e11
+C5_CAPACITY = 2.4e11
 C5_JOBS = 1000
 # Helical triangular lattice with the seven-colour MPKK schedule: the nearest size to
 # 400 x 400 that seven-site domains tile (7 | 402*399, 402 mod 7 = 3), the 400x400
