@@ -98,12 +98,12 @@ C4 = dict(n=256, L_min=100, L_max=1024, f_min=0.1, f_max=0.5, w_min=0.1, w_max=1
 # job mix (C5_CAPACITY attempts/s: the first 1000 jobs of the stream submitted at
 # once, `--workload c5 --rate 1000000`, served at 2.41e11 attempts/s on GB300);
 # the configuration's 10000 jobs take about 10000 x 1.3e10 / (0.8 x C5_CAPACITY)
-# seconds to arrive, so the default run serves the first C5_JOBS of the stream
-# (--c5-jobs 10000 for all of them).
+# seconds (about 12 minutes) to arrive, and the default run serves all of them
+# (--c5-jobs N for the first N of the stream).
 C5 = dict(L_min=64, L_max=2048, f_min=0.1, f_max=0.5, w_min=0.1, w_max=1.2, mcs_min=1e3, mcs_max=1e5,
           seed0=1000000, draw_seed=77, budget=16 << 30)
 C5_CAPACITY = 2.4e11
-C5_JOBS = 1000
+C5_JOBS = 10000
 # Helical triangular lattice with the seven-colour MPKK schedule: the nearest size to
 # 400 x 400 that seven-site domains tile (7 | 402*399, 402 mod 7 = 3), the 400x400
 # workload's composition, omegas and seeds, 2000 MCS (bounded run), histograms every 500.
@@ -679,7 +679,8 @@ def sub_c5(x, n_jobs):
     wait = np.array([r["start_s"] - r["submit_s"] for r in res])
     attempts = sum(r["attempts"] for r in res)
     out = {"value": attempts / makespan, "unit": "attempts/s", "ms_per_step": makespan * 1e3,
-           "config": {"workload": f"serving: Poisson arrivals of the first {len(jobs)} jobs of the 10000-job "
+           "config": {"workload": ("serving: Poisson arrivals of all 10000 jobs of the " if len(jobs) == 10000 else
+                                   f"serving: Poisson arrivals of the first {len(jobs)} jobs of the 10000-job ") +
                                   "stream (side log-uniform 64-2048, A fraction U[0.1,0.5], omega/kT "
                                   "U[0.1,1.2], MCS log-uniform 1e3-1e5, seeds 1e6+j)",
                       "jobs": len(jobs), "arrival_rate_per_s": rate,
